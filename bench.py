@@ -1,0 +1,327 @@
+"""Benchmark of the WENO-theta hot path on GB300.
+
+Workload (one "step" of this benchmark = one whole run of it): 1D Euler, gamma = 1.4,
+N = 4096 cells on [-5, 5], outflow boundaries, seeded Riemann + entropy-wave data,
+CFL 0.5, 2000 TVD-RK3 steps, FP64.  value = cell-updates/s (cells x RK steps / time),
+one cell-update being one cell advanced by a full RK3 step (three RHS evaluations).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs its own independently seeded problem (weak scaling, no
+data exchange); rank 0 prints one JSON line.  --impl reference times the CPU oracle (the
+plain serial reference implementation of the method) on a bounded sample of the workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1504_00731_gb300 import workloads as W  # noqa: E402
+
+METRIC = "FP64 cell-updates/s per GB300 and % HBM roofline; batched & adjoint vs plain"
+N_CELLS = 4096
+RK_STEPS = 2000
+CFL = 0.5
+M = 3
+WORKLOAD = "euler1d_riemann_entropy_N4096_outflow_cfl0.5_2000rk3"
+# Arithmetic of one cell-update (one cell, one RK3 step) of 1D Euler, counted by the oracle's
+# operation-counting instantiation on this workload (tests/test_flop_count.py keeps it honest):
+# +,-,*,/ and sqrt each count one flop.
+FLOPS_PER_CELL_UPDATE = 3696.0
+# Algorithmic HBM bytes of one cell-update: each stage reads u^n and the stage input and
+# writes its output, m doubles each: (2 + 3 + 3) * 8 * m.
+BYTES_PER_CELL_UPDATE = 64.0 * M
+# FP64 peak from unit counts: 152 SMs x 2 FP64 FMA lanes per clock x 2 flops x 2.07 GHz.
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
+L2_FLUSH_BYTES = 256 << 20
+KERNEL_SOURCES = ("wt_kernels.cuh", "wt_math_fast.cuh", "wt_device.cuh")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "stage1d_euler_N4096_traffic.json")
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1504_00731_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_launch():
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary, if the
+    kernel sources are unchanged since it was taken; else None."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            t = json.load(f)
+    except OSError:
+        return None
+    if t.get("kernel_sha") != kernel_hash():
+        return None
+    return t.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline(sample_steps=RK_STEPS):
+    """The oracle, as it stands, on the same workload (serial, one core)."""
+    import oracle as O
+
+    U, x, dx = W.euler_c2(N_CELLS, seed=0)
+    P = O.problem(O.FLUX_EULER1D, bc=O.BC_OUTFLOW)
+    O.lib()
+    t0 = time.perf_counter()
+    _, _, steps = O.run(P, U, dx, cfl=CFL, n_steps=sample_steps)
+    el = time.perf_counter() - t0
+    return {"value": N_CELLS * steps / el, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+            "sample": f"serial C++ oracle (-O2, no FMA contraction), seed-0 workload, {steps} of the {RK_STEPS} RK3 "
+                      f"steps ({el:.2f} s)", "seconds": el}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle as O
+
+    O.lib()
+    sample = 100  # RK steps per benchmark step: a bounded sample of the 2000-step run
+    U, x, dx = W.euler_c2(N_CELLS, seed=0)
+    P = O.problem(O.FLUX_EULER1D, bc=O.BC_OUTFLOW)
+    for _ in range(args.warmup):
+        O.run(P, U, dx, cfl=CFL, n_steps=sample)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        O.run(P, U, dx, cfl=CFL, n_steps=sample)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = N_CELLS * sample * args.steps / tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": N_CELLS, "rk_steps_per_step": sample, "cfl": CFL, "m": M},
+        "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{sample} RK3 steps of the seed-0 workload per benchmark step"},
+        "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+
+    from paper_1504_00731_gb300 import binding as B
+    from paper_1504_00731_gb300 import build as BLD
+
+    world, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    if rank == 0:
+        BLD.build_library()
+    if world > 1:
+        dist.barrier()
+    B.lib()
+
+    U0, x, dx = W.euler_c2(N_CELLS, seed=rank)
+    prob = B.problem(B.WT_FLUX_EULER1D, bc=B.WT_BC_OUTFLOW, mode=B.WT_MODE_FAST)
+    grid = B.grid_1d(N_CELLS, -5.0, 5.0)
+    ws = B.alloc_workspace(B.workspace_bytes(prob, grid), dev)
+    u_src = torch.from_numpy(U0).to(dev)
+    u = torch.empty_like(u_src)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def one_run(u_arr):
+        return B.weno_theta_step(prob, grid, u_arr, CFL, ws, max_steps=RK_STEPS)
+
+    for _ in range(args.warmup):
+        u.copy_(u_src)
+        one_run(u)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- device-resident timed region: K whole runs, L2 flushed between them (not timed)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        barrier()
+        wall0 = time.perf_counter()
+        for k in range(args.steps):
+            u.copy_(u_src)
+            flush.zero_()
+            ev[k][0].record(stream)
+            t_reached, nsteps = one_run(u)
+            ev[k][1].record(stream)
+            assert nsteps == RK_STEPS
+        barrier()
+        wall = time.perf_counter() - wall0
+    ms = [a.elapsed_time(b) for a, b in ev]
+    tot_ms = float(sum(ms))
+    if world > 1:
+        t = torch.tensor([tot_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    ms_per_step = tot_ms / args.steps
+    cell_updates = N_CELLS * RK_STEPS
+    value = world * cell_updates / (ms_per_step * 1e-3)
+
+    # ---- end to end through the public API with pinned host buffers (copies inside)
+    h_src = torch.from_numpy(U0.copy()).pin_memory()
+    h_u = torch.empty_like(h_src).pin_memory()
+    e2e_ms = []
+    barrier()
+    for k in range(max(2, min(args.steps, 5))):
+        h_u.copy_(h_src)
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        B.weno_theta_step(prob, grid, h_u.numpy(), CFL, ws, max_steps=RK_STEPS, stream=stream.cuda_stream)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_t = float(np.mean(e2e_ms))
+    if world > 1:
+        t = torch.tensor([e2e_t], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_t = float(t.item())
+    e2e_value = world * cell_updates / (e2e_t * 1e-3)
+
+    if rank == 0:
+        peaks = measured_peaks()
+        launches_per_run = 3 * RK_STEPS
+        stage_launch_s = (ms_per_step * 1e-3) / launches_per_run
+        flops_per_launch = FLOPS_PER_CELL_UPDATE / 3.0 * N_CELLS
+        achieved = flops_per_launch / stage_launch_s / 1e9
+        hbm_gbs = BYTES_PER_CELL_UPDATE / 3.0 * N_CELLS / stage_launch_s / 1e9
+        hbm_peak = peaks.get("hbm_gbs", 6800.0)
+        line = {
+            "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": N_CELLS, "rk_steps": RK_STEPS, "m": M, "cfl": CFL,
+                       "bc": "outflow", "mode": "fast", "alpha_R": 50.0, "eps": 1e-10,
+                       "l2": "flushed between timed runs (256 MiB write, untimed)",
+                       "parallelism": f"replicas: one seeded problem per GPU ({world})"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                         "frac": achieved / FP64_PEAK_GFLOPS, "traffic": traffic_per_launch(),
+                         "kernel": "stage1d_kernel<FastMath, Euler1D> (3 launches per RK step)",
+                         "peak_source": "152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz (unit counts and max clock)",
+                         "hbm": {"achieved_gbs": hbm_gbs, "peak_gbs": hbm_peak, "frac": hbm_gbs / hbm_peak,
+                                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}},
+            "e2e": {"value": e2e_value, "unit": "cell-updates/s", "h2d_bytes_per_step": int(U0.nbytes),
+                    "d2h_bytes_per_step": int(U0.nbytes)},
+            "gpu_launches": args.steps * (launches_per_run + 3),
+            "clocks": clk.summary(),
+            "wall_s_timed_region": wall,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

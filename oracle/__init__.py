@@ -100,6 +100,7 @@ def lib():
     L.wto_run.argtypes = [PP, I64, I64, D, D, P, D, D, D, I64, P, PI64]
     L.wto_run_jvp.argtypes = [PP, I64, I64, D, D, P, P, D, D, D, I64, P, PI64]
     L.wto_count_rhs_ops.argtypes = [PP, I64, I64, D, D, P, PI64]
+    L.wto_count_run_ops.argtypes = [PP, I64, I64, D, D, P, D, I64, PI64]
     L.wto_riemann_star.argtypes = [D, D, D, D, D, D, D, P, P, PI32]
     L.wto_riemann_sample.argtypes = [D, D, D, D, D, D, D, D, D, P, I64, P, P, P]
     _lib = L
@@ -205,6 +206,15 @@ def count_rhs_ops(prob, u, dx, dy=1.0):
     u, nx, ny = _dims(u)
     out = np.zeros(5, dtype=np.int64)
     lib().wto_count_rhs_ops(ctypes.byref(prob), nx, ny, dx, dy, _ptr(u),
+                            out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
+    return dict(zip(("add", "mul", "div", "sqrt", "cmp"), (int(x) for x in out)))
+
+
+def count_run_ops(prob, u, dx, dy=1.0, cfl=0.5, n_steps=1):
+    """Arithmetic operations of n_steps RK3 steps, CFL step included (add counts subtractions)."""
+    u, nx, ny = _dims(u)
+    out = np.zeros(5, dtype=np.int64)
+    lib().wto_count_run_ops(ctypes.byref(prob), nx, ny, dx, dy, _ptr(u), cfl, n_steps,
                             out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
     return dict(zip(("add", "mul", "div", "sqrt", "cmp"), (int(x) for x in out)))
 

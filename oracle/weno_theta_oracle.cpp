@@ -805,6 +805,22 @@ void wto_count_rhs_ops(const Problem* P, int64_t nx, int64_t ny, double dx, doub
   out[4] = g_ops.cmp;
 }
 
+/* Arithmetic operations of n_steps RK3 steps (CFL step from u^n included). */
+void wto_count_run_ops(const Problem* P, int64_t nx, int64_t ny, double dx, double dy, const double* u, double cfl,
+                       int64_t n_steps, int64_t* out) {
+  Grid g{nx, ny, dx, dy};
+  size_t len = (size_t)P->m * nx * ny;
+  std::vector<Cnt> U(len);
+  for (size_t j = 0; j < len; ++j) U[j] = Cnt(u[j]);
+  g_ops = OpCount{0, 0, 0, 0, 0};
+  run(*P, g, U.data(), cfl, 0.0, INFINITY, n_steps, (double*)0, (int64_t*)0);
+  out[0] = g_ops.add;
+  out[1] = g_ops.mul;
+  out[2] = g_ops.div;
+  out[3] = g_ops.sqrt;
+  out[4] = g_ops.cmp;
+}
+
 /* Exact Riemann problem: star state and the solution sampled at xs (jump at x0, time t). */
 void wto_riemann_star(double rL, double uL, double pL, double rR, double uR, double pR, double gamma, double* pstar,
                       double* ustar, int32_t* iters) {

@@ -1,0 +1,433 @@
+// C ABI of the WENO-theta library (include/weno_theta.h): argument checks, workspace
+// layout, host <-> device staging, and the RK step loop replayed from a CUDA graph.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "wt_launch.h"
+
+namespace {
+
+using namespace wt;
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define WT_CUDA(call)                                                                          \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess) return fail(WT_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+
+int expected_m(int flux) {
+  switch (flux) {
+    case WT_FLUX_ADVECTION:
+    case WT_FLUX_BURGERS: return 1;
+    case WT_FLUX_EULER1D: return 3;
+    case WT_FLUX_EULER2D: return 4;
+  }
+  return -1;
+}
+
+bool bc_ok(int b) { return b == WT_BC_PERIODIC || b == WT_BC_OUTFLOW || b == WT_BC_REFLECTIVE; }
+
+int check_problem(const wt_problem* p) {
+  if (!p) return fail(WT_ERR_ARG, "problem is NULL");
+  if (expected_m(p->flux) < 0) return fail(WT_ERR_ARG, "unknown flux %d", p->flux);
+  if (p->m != expected_m(p->flux)) return fail(WT_ERR_ARG, "m = %d does not match flux %d", p->m, p->flux);
+  if (p->mode != WT_MODE_FAST && p->mode != WT_MODE_STRICT) return fail(WT_ERR_ARG, "unknown mode %d", p->mode);
+  if (p->reserved != 0) return fail(WT_ERR_ARG, "reserved field must be 0");
+  if (!(p->eps > 0.0) || !std::isfinite(p->eps)) return fail(WT_ERR_ARG, "eps must be positive");
+  if (!(p->alpha_R >= 0.0)) return fail(WT_ERR_ARG, "alpha_R must be >= 0");
+  if ((p->flux == WT_FLUX_EULER1D || p->flux == WT_FLUX_EULER2D) && !(p->gamma > 1.0))
+    return fail(WT_ERR_ARG, "gamma must exceed 1");
+  if (p->flux == WT_FLUX_ADVECTION && !std::isfinite(p->adv_speed)) return fail(WT_ERR_ARG, "adv_speed not finite");
+  for (int d = 0; d < 2; ++d)
+    if (!bc_ok(p->bc_lo[d]) || !bc_ok(p->bc_hi[d])) return fail(WT_ERR_ARG, "unknown boundary condition");
+  if ((p->flux == WT_FLUX_ADVECTION || p->flux == WT_FLUX_BURGERS) &&
+      (p->bc_lo[0] == WT_BC_REFLECTIVE || p->bc_hi[0] == WT_BC_REFLECTIVE))
+    return fail(WT_ERR_UNSUPPORTED, "reflective boundaries are defined for the Euler equations only");
+  if ((p->bc_lo[0] == WT_BC_PERIODIC) != (p->bc_hi[0] == WT_BC_PERIODIC))
+    return fail(WT_ERR_ARG, "a periodic boundary must be periodic at both ends");
+  return WT_OK;
+}
+
+int check_grid_1d(const wt_problem* p, const wt_grid* g) {
+  if (!g) return fail(WT_ERR_ARG, "grid is NULL");
+  if (g->reserved != 0) return fail(WT_ERR_ARG, "reserved field must be 0");
+  if (p->flux == WT_FLUX_EULER2D) return fail(WT_ERR_UNSUPPORTED, "2D Euler is not available in this build");
+  if (g->ndim != 1) return fail(WT_ERR_ARG, "ndim must be 1 for a 1D flux");
+  if (g->n[0] < G) return fail(WT_ERR_ARG, "n = %lld is below the minimum of %d cells", (long long)g->n[0], G);
+  if (g->n[0] > (1LL << 40)) return fail(WT_ERR_ARG, "n too large");
+  if (!(g->hi[0] > g->lo[0]) || !std::isfinite(g->hi[0] - g->lo[0])) return fail(WT_ERR_ARG, "need lo < hi");
+  return WT_OK;
+}
+
+// padded plane stride: n + 2G rounded up to 32 doubles (256 bytes)
+inline long long plane_pitch(long long n) { return ((n + 2 * G + 31) / 32) * 32; }
+
+// 1D workspace: [Ctl][Un][U1][U2][staging m*n][staging m*n]
+struct Layout1D {
+  size_t ctl, un, u1, u2, st_in, st_out, total;
+  long long pitch;
+};
+
+Layout1D layout_1d(int m, long long n) {
+  Layout1D L;
+  L.pitch = plane_pitch(n);
+  const size_t plane = (size_t)m * L.pitch * sizeof(double);
+  const size_t stage = (size_t)m * n * sizeof(double);
+  size_t o = 0;
+  L.ctl = o;
+  o = align_up(o + sizeof(Ctl));
+  L.un = o;
+  o = align_up(o + plane);
+  L.u1 = o;
+  o = align_up(o + plane);
+  L.u2 = o;
+  o = align_up(o + plane);
+  L.st_in = o;
+  o = align_up(o + stage);
+  L.st_out = o;
+  o = align_up(o + stage);
+  L.total = o;
+  return L;
+}
+
+// Device of a pointer, and whether it is device-accessible memory (device or managed).
+int pointer_info(const void* p, bool* is_device, int* device) {
+  cudaPointerAttributes attr;
+  cudaError_t e = cudaPointerGetAttributes(&attr, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *is_device = false;
+    *device = -1;
+    return WT_OK;
+  }
+  *is_device = (attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged);
+  *device = attr.device;
+  return WT_OK;
+}
+
+// Makes the workspace's device current for the duration of a call.
+struct DeviceGuard {
+  int old = -1;
+  bool changed = false;
+  int enter(int dev) {
+    if (cudaGetDevice(&old) != cudaSuccess) return fail(WT_ERR_CUDA, "cudaGetDevice failed");
+    if (dev >= 0 && dev != old) {
+      if (cudaSetDevice(dev) != cudaSuccess) return fail(WT_ERR_CUDA, "cudaSetDevice(%d) failed", dev);
+      changed = true;
+    }
+    return WT_OK;
+  }
+  ~DeviceGuard() {
+    if (changed) cudaSetDevice(old);
+  }
+};
+
+int check_ws(void* ws, size_t ws_bytes, size_t need, int* device) {
+  if (!ws) return fail(WT_ERR_WORKSPACE, "workspace is NULL");
+  if ((reinterpret_cast<uintptr_t>(ws) & (kAlign - 1)) != 0) return fail(WT_ERR_WORKSPACE, "workspace not 256-byte aligned");
+  if (ws_bytes < need) return fail(WT_ERR_WORKSPACE, "workspace has %zu bytes, needs %zu", ws_bytes, need);
+  bool dev;
+  pointer_info(ws, &dev, device);
+  if (!dev) return fail(WT_ERR_WORKSPACE, "workspace is not device memory");
+  return WT_OK;
+}
+
+int default_tile(int flux, long long n) {
+  if (flux == WT_FLUX_EULER1D) {
+    // about one CTA per SM for short grids, larger tiles once the grid fills the GPU
+    if (n <= 152LL * 31) return 31;
+    if (n <= 152LL * 4 * 63) return 63;
+    return 127;
+  }
+  return n <= 152LL * 2 * 63 ? 63 : 127;
+}
+
+Stage1DArgs base_args(const wt_problem* p, long long n, double dx, long long pitch, Ctl* ctl) {
+  Stage1DArgs a;
+  memset(&a, 0, sizeof a);
+  a.n = n;
+  a.pitch = pitch;
+  a.lout_stride = n;
+  a.dx = dx;
+  a.inv_dx = 1.0 / dx;
+  a.gamma = p->gamma;
+  a.adv_speed = p->adv_speed;
+  a.eps = p->eps;
+  a.alpha_R = p->alpha_R;
+  a.bc_lo = p->bc_lo[0];
+  a.bc_hi = p->bc_hi[0];
+  a.ctl = ctl;
+  return a;
+}
+
+cudaError_t launch_stage(const wt_problem* p, int stage, int tile, const Stage1DArgs& a, cudaStream_t st) {
+  return p->mode == WT_MODE_STRICT ? launch_stage1d_strict(p->flux, stage, tile, a, st)
+                                   : launch_stage1d_fast(p->flux, stage, tile, a, st);
+}
+
+cudaError_t launch_alpha(const wt_problem* p, const double* u, long long n, long long pitch, Ctl* ctl, int slot,
+                         cudaStream_t st) {
+  return p->mode == WT_MODE_STRICT ? launch_alpha1d_strict(p->flux, u, n, pitch, p->gamma, p->adv_speed, ctl, slot, st)
+                                   : launch_alpha1d_fast(p->flux, u, n, pitch, p->gamma, p->adv_speed, ctl, slot, st);
+}
+
+// Copies the caller's state (host or device) into the padded planes with ghost cells.
+int stage_in(const double* u, bool u_dev, double* staging, int m, long long n, long long pitch, double* Un,
+             int bc_lo, int bc_hi, cudaStream_t st) {
+  const double* src = u;
+  if (!u_dev) {
+    WT_CUDA(cudaMemcpyAsync(staging, u, sizeof(double) * m * n, cudaMemcpyHostToDevice, st));
+    src = staging;
+  }
+  WT_CUDA(launch_pack1d(src, n, Un, n, pitch, m, bc_lo, bc_hi, 1, st));
+  return WT_OK;
+}
+
+// --- CUDA graph of one RK step (three fused stage launches), cached per argument set
+struct GraphEntry {
+  Stage1DArgs a[3];
+  int flux, mode, tile, device;
+  cudaGraphExec_t exec;
+};
+std::mutex g_graph_mu;
+std::vector<GraphEntry> g_graphs;
+cudaStream_t g_capture_stream[64] = {};
+
+bool same_args(const Stage1DArgs& x, const Stage1DArgs& y) { return memcmp(&x, &y, sizeof x) == 0; }
+
+int get_step_graph(const wt_problem* p, int device, int tile, const Stage1DArgs a[3], cudaGraphExec_t* out) {
+  std::lock_guard<std::mutex> lk(g_graph_mu);
+  for (auto& e : g_graphs) {
+    if (e.device == device && e.flux == p->flux && e.mode == p->mode && e.tile == tile && same_args(e.a[0], a[0]) &&
+        same_args(e.a[1], a[1]) && same_args(e.a[2], a[2])) {
+      *out = e.exec;
+      return WT_OK;
+    }
+  }
+  if (device < 0 || device >= 64) return fail(WT_ERR_CUDA, "device index %d out of range", device);
+  cudaStream_t& cs = g_capture_stream[device];
+  if (!cs) WT_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  WT_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  cudaError_t le = cudaSuccess;
+  for (int s = 0; s < 3 && le == cudaSuccess; ++s) le = launch_stage(p, s, tile, a[s], cs);
+  cudaGraph_t graph = nullptr;
+  cudaError_t ee = cudaStreamEndCapture(cs, &graph);
+  if (le != cudaSuccess) return fail(WT_ERR_CUDA, "stage launch during capture: %s", cudaGetErrorString(le));
+  if (ee != cudaSuccess) return fail(WT_ERR_CUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(ee));
+  cudaGraphExec_t exec = nullptr;
+  cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ie != cudaSuccess) return fail(WT_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(ie));
+  if (g_graphs.size() >= 16) {
+    cudaGraphExecDestroy(g_graphs.front().exec);
+    g_graphs.erase(g_graphs.begin());
+  }
+  GraphEntry e;
+  e.a[0] = a[0];
+  e.a[1] = a[1];
+  e.a[2] = a[2];
+  e.flux = p->flux;
+  e.mode = p->mode;
+  e.tile = tile;
+  e.device = device;
+  e.exec = exec;
+  g_graphs.push_back(e);
+  *out = exec;
+  return WT_OK;
+}
+
+Ctl make_ctl(double cfl, double dt_fixed, double t_final) {
+  Ctl h;
+  memset(&h, 0, sizeof h);
+  h.t = 0.0;
+  h.t_final = t_final;
+  h.cfl = cfl;
+  h.dt_fixed = dt_fixed;
+  h.active = 1;
+  return h;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* wt_last_error(void) { return g_err.c_str(); }
+
+size_t wt_workspace_bytes(const wt_problem* prob, const wt_grid* grid, int64_t batch_cells, int32_t nprob) {
+  if (check_problem(prob) != WT_OK) return 0;
+  if (grid) {
+    if (check_grid_1d(prob, grid) != WT_OK) return 0;
+    return layout_1d(prob->m, grid->n[0]).total;
+  }
+  (void)batch_cells;
+  (void)nprob;
+  fail(WT_ERR_UNSUPPORTED, "batched workspace is not available in this build");
+  return 0;
+}
+
+int weno_theta_rhs(const wt_problem* prob, const wt_grid* grid, const double* u, double* L, void* ws, size_t ws_bytes,
+                   void* stream) {
+  int rc;
+  if ((rc = check_problem(prob)) != WT_OK) return rc;
+  if ((rc = check_grid_1d(prob, grid)) != WT_OK) return rc;
+  if (!u || !L) return fail(WT_ERR_ARG, "u and L must not be NULL");
+  const int m = prob->m;
+  const long long n = grid->n[0];
+  const Layout1D lay = layout_1d(m, n);
+  int dev;
+  if ((rc = check_ws(ws, ws_bytes, lay.total, &dev)) != WT_OK) return rc;
+  DeviceGuard guard;
+  if ((rc = guard.enter(dev)) != WT_OK) return rc;
+  bool u_dev, L_dev;
+  int d_u, d_L;
+  pointer_info(u, &u_dev, &d_u);
+  pointer_info(L, &L_dev, &d_L);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char* w = static_cast<char*>(ws);
+  Ctl* ctl = reinterpret_cast<Ctl*>(w + lay.ctl);
+  double* Un = reinterpret_cast<double*>(w + lay.un);
+  double* st_in = reinterpret_cast<double*>(w + lay.st_in);
+  double* st_out = reinterpret_cast<double*>(w + lay.st_out);
+  const double dx = (grid->hi[0] - grid->lo[0]) / (double)n;
+
+  WT_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl), st));
+  if ((rc = stage_in(u, u_dev, st_in, m, n, lay.pitch, Un, prob->bc_lo[0], prob->bc_hi[0], st)) != WT_OK) return rc;
+  WT_CUDA(launch_alpha(prob, Un, n, lay.pitch, ctl, 0, st));
+  Stage1DArgs a = base_args(prob, n, dx, lay.pitch, ctl);
+  a.uin = Un;
+  a.Lout = L_dev ? L : st_out;
+  WT_CUDA(launch_stage(prob, STAGE_RHS, default_tile(prob->flux, n), a, st));
+  if (!L_dev) {
+    WT_CUDA(cudaMemcpyAsync(L, st_out, sizeof(double) * m * n, cudaMemcpyDeviceToHost, st));
+  }
+  if (!u_dev || !L_dev) {
+    WT_CUDA(cudaStreamSynchronize(st));
+    int status = 0;
+    WT_CUDA(cudaMemcpy(&status, &ctl->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (status != 0) return fail(status, "device reported status %d (non-physical state or NaN)", status);
+  }
+  return WT_OK;
+}
+
+int weno_theta_step(const wt_problem* prob, const wt_grid* grid, double* u, double cfl, double dt_fixed,
+                    double t_final, int64_t max_steps, double* t_reached, int64_t* steps, void* ws, size_t ws_bytes,
+                    void* stream) {
+  int rc;
+  if ((rc = check_problem(prob)) != WT_OK) return rc;
+  if ((rc = check_grid_1d(prob, grid)) != WT_OK) return rc;
+  if (!u) return fail(WT_ERR_ARG, "u must not be NULL");
+  if (max_steps < 0) return fail(WT_ERR_ARG, "max_steps must be >= 0");
+  if (!(dt_fixed > 0.0) && !(cfl > 0.0 && std::isfinite(cfl))) return fail(WT_ERR_ARG, "need cfl > 0 or dt_fixed > 0");
+  if (!(t_final > 0.0) && !(t_final == 0.0)) return fail(WT_ERR_ARG, "t_final must be >= 0");
+  const int m = prob->m;
+  const long long n = grid->n[0];
+  const Layout1D lay = layout_1d(m, n);
+  int dev;
+  if ((rc = check_ws(ws, ws_bytes, lay.total, &dev)) != WT_OK) return rc;
+  DeviceGuard guard;
+  if ((rc = guard.enter(dev)) != WT_OK) return rc;
+  bool u_dev;
+  int d_u;
+  pointer_info(u, &u_dev, &d_u);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char* w = static_cast<char*>(ws);
+  Ctl* ctl = reinterpret_cast<Ctl*>(w + lay.ctl);
+  double* Un = reinterpret_cast<double*>(w + lay.un);
+  double* U1 = reinterpret_cast<double*>(w + lay.u1);
+  double* U2 = reinterpret_cast<double*>(w + lay.u2);
+  double* st_in = reinterpret_cast<double*>(w + lay.st_in);
+  const double dx = (grid->hi[0] - grid->lo[0]) / (double)n;
+  const int tile = default_tile(prob->flux, n);
+
+  const Ctl h = make_ctl(cfl, dt_fixed, t_final);
+  WT_CUDA(cudaMemcpyAsync(ctl, &h, sizeof(Ctl), cudaMemcpyHostToDevice, st));
+  if ((rc = stage_in(u, u_dev, st_in, m, n, lay.pitch, Un, prob->bc_lo[0], prob->bc_hi[0], st)) != WT_OK) return rc;
+  WT_CUDA(launch_alpha(prob, Un, n, lay.pitch, ctl, 0, st));
+
+  Stage1DArgs a[3];
+  for (int s = 0; s < 3; ++s) a[s] = base_args(prob, n, dx, lay.pitch, ctl);
+  a[0].uin = Un;
+  a[0].uout = U1;
+  a[1].uin = U1;
+  a[1].un = Un;
+  a[1].uout = U2;
+  a[2].uin = U2;
+  a[2].un = Un;
+  a[2].uout = Un;
+  cudaGraphExec_t exec;
+  if (max_steps > 0 && (rc = get_step_graph(prob, dev, tile, a, &exec)) != WT_OK) return rc;
+
+  Ctl hc;
+  int64_t launched = 0;
+  const bool bounded_time = std::isfinite(t_final);
+  const int64_t chunk = bounded_time ? 64 : max_steps;
+  while (launched < max_steps) {
+    int64_t k = max_steps - launched;
+    if (k > chunk) k = chunk;
+    for (int64_t i = 0; i < k; ++i) WT_CUDA(cudaGraphLaunch(exec, st));
+    launched += k;
+    if (bounded_time) {
+      WT_CUDA(cudaMemcpyAsync(&hc, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+      WT_CUDA(cudaStreamSynchronize(st));
+      if (hc.status != 0 || !(hc.t < hc.t_final)) break;
+    }
+  }
+  WT_CUDA(cudaMemcpyAsync(&hc, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+  WT_CUDA(cudaStreamSynchronize(st));
+  if (hc.status != 0) return fail(hc.status, "device reported status %d after %lld steps", hc.status, hc.steps);
+  if (u_dev) {
+    WT_CUDA(launch_unpack1d(Un, lay.pitch, u, n, n, m, st));
+  } else {
+    WT_CUDA(launch_unpack1d(Un, lay.pitch, st_in, n, n, m, st));
+    WT_CUDA(cudaMemcpyAsync(u, st_in, sizeof(double) * m * n, cudaMemcpyDeviceToHost, st));
+  }
+  WT_CUDA(cudaStreamSynchronize(st));
+  if (t_reached) *t_reached = hc.t;
+  if (steps) *steps = hc.steps;
+  return WT_OK;
+}
+
+int weno_theta_step_batched(const wt_problem* prob, const wt_segment* segs, int32_t nprob, double* u_packed,
+                            int64_t total, double cfl, int64_t n_steps, double* t_per_problem, void* ws,
+                            size_t ws_bytes, void* stream) {
+  (void)prob; (void)segs; (void)nprob; (void)u_packed; (void)total; (void)cfl; (void)n_steps; (void)t_per_problem;
+  (void)ws; (void)ws_bytes; (void)stream;
+  return fail(WT_ERR_UNSUPPORTED, "batched stepping is not available in this build");
+}
+
+size_t wt_adjoint_workspace_bytes(const wt_problem* prob, const wt_grid* grid, int64_t n_steps,
+                                  int32_t checkpoint_every) {
+  (void)prob; (void)grid; (void)n_steps; (void)checkpoint_every;
+  fail(WT_ERR_UNSUPPORTED, "the adjoint is not available in this build");
+  return 0;
+}
+
+int weno_theta_adjoint(const wt_problem* prob, const wt_grid* grid, const double* u0, double cfl, int64_t n_steps,
+                       int32_t checkpoint_every, const double* dJ_duT, double* dJ_du0, double* uT, void* ws,
+                       size_t ws_bytes, void* stream) {
+  (void)prob; (void)grid; (void)u0; (void)cfl; (void)n_steps; (void)checkpoint_every; (void)dJ_duT; (void)dJ_du0;
+  (void)uT; (void)ws; (void)ws_bytes; (void)stream;
+  return fail(WT_ERR_UNSUPPORTED, "the adjoint is not available in this build");
+}
+
+}  // extern "C"

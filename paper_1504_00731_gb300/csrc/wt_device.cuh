@@ -1,0 +1,135 @@
+// Device-side building blocks shared by the WENO-theta kernels: the control block kept in
+// the workspace, bulk-copy (TMA) staging with bounded mbarrier waits, block-wide maxima,
+// and ghost-cell index maps.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/weno_theta.h"
+
+namespace wt {
+
+constexpr int G = 3;  // ghost cells per side: the stencil of an interface is {j-2 .. j+3}
+
+// Per-run control block, resident in the workspace.  Lax-Friedrichs constants are kept
+// as the bit patterns of non-negative doubles so that atomicMax on unsigned 64-bit
+// integers is an exact maximum.  A ring of three slots lets stage s read slot s, fill
+// slot s+1 and clear slot s+2 without a separate launch.
+struct Ctl {
+  unsigned long long amax[3][8];  // [slot][dir * 4 + field]
+  unsigned long long cfl2d[3];    // 2D: max_j ((|u|+c)/dx + (|v|+c)/dy) per slot
+  double t;                       // time reached
+  double dt;                      // step of the current RK step
+  double t_final;
+  double cfl;
+  double dt_fixed;
+  long long steps;
+  int status;                     // first device-detected failure (wt_status), 0 if none
+  int active;                     // 1 while the current step is being taken
+  int pad[2];
+};
+
+__device__ __forceinline__ void flag_error(Ctl* ctl, int code) {
+  if (ctl) atomicCAS(&ctl->status, 0, code);
+}
+
+// ---------------------------------------------------------------------------------------
+// Bulk copies global -> shared (cp.async.bulk, completion on an mbarrier)
+// ---------------------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// dst, src 16-byte aligned; bytes a multiple of 16
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: gives up after ~2^31 SM clock cycles (about one second).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  const long long start = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - start > (1LL << 31)) return false;
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------------------
+// Block-wide maxima of non-negative doubles (bit patterns order like the values)
+// ---------------------------------------------------------------------------------------
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    double w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = (v < w) ? w : v;
+  }
+  return v;
+}
+
+// Reduces K values per thread to the block maximum and folds it into dst[k] with one
+// atomicMax per block.  scratch: >= K * 32 doubles of shared memory.
+template <int K>
+__device__ __forceinline__ void block_max_atomic(double (&v)[K], double* scratch, unsigned long long* dst) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double w = warp_max(v[k]);
+    if (lane == 0) scratch[k * 32 + warp] = w;
+  }
+  __syncthreads();
+  if (threadIdx.x < K) {
+    double m = 0.0;
+    for (int w = 0; w < nw; ++w) {
+      double x = scratch[threadIdx.x * 32 + w];
+      m = (m < x) ? x : m;
+    }
+    if (m > 0.0 || m == 0.0) atomicMax(&dst[threadIdx.x], (unsigned long long)__double_as_longlong(m));
+  }
+}
+
+__device__ __forceinline__ double bits_to_double(unsigned long long b) { return __longlong_as_double((long long)b); }
+
+// ---------------------------------------------------------------------------------------
+// Ghost cells: interior index of the cell whose value ghost index g (g < 0 or g >= n)
+// takes, and whether the normal momentum flips sign.
+// ---------------------------------------------------------------------------------------
+
+__device__ __forceinline__ long long ghost_source(long long g, long long n, int bc_lo, int bc_hi, bool* flip) {
+  *flip = false;
+  if (g < 0) {
+    if (bc_lo == WT_BC_PERIODIC) return g + n;
+    if (bc_lo == WT_BC_OUTFLOW) return 0;
+    *flip = true;
+    return -g - 1;
+  }
+  if (bc_hi == WT_BC_PERIODIC) return g - n;
+  if (bc_hi == WT_BC_OUTFLOW) return n - 1;
+  *flip = true;
+  return 2 * n - 1 - g;
+}
+
+}  // namespace wt

@@ -1,0 +1,64 @@
+// Fast-arithmetic instantiations of the 1D kernels, plus the boundary-fill (pack) and
+// unpack kernels, which do no arithmetic.
+#include "wt_kernels.cuh"
+#include "wt_math_fast.cuh"
+
+namespace wt {
+
+__global__ void pack1d_kernel(const double* __restrict__ src, long long src_stride, double* __restrict__ dst,
+                              long long n, long long pitch, int m, int bc_lo, int bc_hi, int flip_comp) {
+  const long long row = n + 2 * G;
+  const long long total = (long long)m * row;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(idx / row);
+    const long long p = idx - (long long)c * row;
+    const long long j = p - G;
+    bool flip = false;
+    const long long sj = (j >= 0 && j < n) ? j : ghost_source(j, n, bc_lo, bc_hi, &flip);
+    double v = src[c * src_stride + sj];
+    if (flip && c == flip_comp) v = -v;
+    dst[c * pitch + p] = v;
+  }
+}
+
+__global__ void unpack1d_kernel(const double* __restrict__ src, long long pitch, double* __restrict__ dst,
+                                long long dst_stride, long long n, int m) {
+  const long long total = (long long)m * n;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(idx / n);
+    const long long j = idx - (long long)c * n;
+    dst[c * dst_stride + j] = src[c * pitch + j + G];
+  }
+}
+
+static unsigned copy_grid(long long total) {
+  long long b = (total + 255) / 256;
+  if (b > 4864) b = 4864;
+  return (unsigned)(b < 1 ? 1 : b);
+}
+
+cudaError_t launch_pack1d(const double* src, long long src_stride, double* dst, long long n, long long pitch, int m,
+                          int bc_lo, int bc_hi, int flip_comp, cudaStream_t st) {
+  pack1d_kernel<<<copy_grid((long long)m * (n + 2 * G)), 256, 0, st>>>(src, src_stride, dst, n, pitch, m, bc_lo, bc_hi,
+                                                                         flip_comp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unpack1d(const double* src, long long pitch, double* dst, long long dst_stride, long long n, int m,
+                            cudaStream_t st) {
+  unpack1d_kernel<<<copy_grid((long long)m * n), 256, 0, st>>>(src, pitch, dst, dst_stride, n, m);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stage1d_fast(int flux, int stage, int tile, const Stage1DArgs& a, cudaStream_t st) {
+  return launch_stage1d_policy<FastMath>(flux, stage, tile, a, st);
+}
+
+cudaError_t launch_alpha1d_fast(int flux, const double* u, long long n, long long pitch, double gamma, double adv,
+                                Ctl* ctl, int slot, cudaStream_t st) {
+  return launch_alpha1d_policy<FastMath>(flux, u, n, pitch, gamma, adv, ctl, slot, st);
+}
+
+}  // namespace wt

@@ -1,0 +1,17 @@
+// Strict-arithmetic instantiations of the 1D kernels.  Built with -fmad=false: no operation
+// is contracted, so every result equals a literal binary64 evaluation of the paper's formulas.
+#include "wt_kernels.cuh"
+#include "wt_math_strict.cuh"
+
+namespace wt {
+
+cudaError_t launch_stage1d_strict(int flux, int stage, int tile, const Stage1DArgs& a, cudaStream_t st) {
+  return launch_stage1d_policy<StrictMath>(flux, stage, tile, a, st);
+}
+
+cudaError_t launch_alpha1d_strict(int flux, const double* u, long long n, long long pitch, double gamma, double adv,
+                                  Ctl* ctl, int slot, cudaStream_t st) {
+  return launch_alpha1d_policy<StrictMath>(flux, u, n, pitch, gamma, adv, ctl, slot, st);
+}
+
+}  // namespace wt

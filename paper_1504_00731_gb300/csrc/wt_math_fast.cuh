@@ -1,0 +1,167 @@
+// Fast arithmetic policy.  Same mathematics as the strict policy, rearranged for a GPU
+// whose FP64 pipe is its scarce resource (about 2 FMA per clock per SM on GB300, with
+// integer and FP32 pipes 30-60x wider):
+//   - fused multiply-adds throughout;
+//   - the indicators of Eqs. (be0_cen)-(be3_cen), (tau_5), (tau_6) from first and second
+//     differences of the stencil, which share most of their terms;
+//   - comparisons of non-negative doubles on their bit patterns (integer pipe);
+//   - the weights of Eq. (om) over a common denominator prod_l (eps + beta_l), so one
+//     division per reconstruction; a restricted stencil (all beta = 0, Eq. (be_res)) has
+//     weights equal to gamma^theta and takes the linear combination directly;
+//   - the restriction test R(beta) <= alpha_R as max beta <= alpha_R (eps + min beta);
+//   - the 1/2 of the flux splitting folded into the left eigenvectors.
+// Results agree with the strict policy to rounding.
+#pragma once
+
+#include "wt_device.cuh"
+
+namespace wt {
+
+struct FastMath {
+  static constexpr bool kStrict = false;
+
+  __device__ __forceinline__ static long long bits(double x) { return __double_as_longlong(x); }
+  // max / min / less-than of non-negative doubles through their bit patterns
+  __device__ __forceinline__ static double nmax(double a, double b) { return bits(a) < bits(b) ? b : a; }
+  __device__ __forceinline__ static double nmin(double a, double b) { return bits(b) < bits(a) ? b : a; }
+
+  __device__ __forceinline__ static double flux_advection(double a, double u) { return a * u; }
+  __device__ __forceinline__ static double flux_burgers(double u) { return 0.5 * u * u; }
+
+  __device__ __forceinline__ static void euler_cell(const double* U, double gamma, double* f, double& u, double& H,
+                                                    double& sr, double& p) {
+    const double ir = 1.0 / U[0];
+    u = U[1] * ir;
+    p = (gamma - 1.0) * fma(-0.5 * U[1], u, U[2]);
+    const double e = U[2] + p;
+    f[0] = U[1];
+    f[1] = fma(U[1], u, p);
+    f[2] = e * u;
+    H = e * ir;
+    sr = sqrt(U[0]);
+  }
+
+  __device__ __forceinline__ static double euler_speeds(const double* U, double gamma, double* lam) {
+    const double ir = 1.0 / U[0];
+    const double u = U[1] * ir;
+    const double p = (gamma - 1.0) * fma(-0.5 * U[1], u, U[2]);
+    const double c = sqrt(gamma * p * ir);
+    lam[0] = fabs(u - c);
+    lam[1] = fabs(u);
+    lam[2] = fabs(u + c);
+    return p;
+  }
+
+  // L is stored pre-scaled by 1/2 (the factor of Eq. (flux_split_lf))
+  __device__ __forceinline__ static void roe(double sa, double ua, double Ha, double sb, double ub, double Hb,
+                                             double gamma, double* L, double* rs) {
+    const double is = 1.0 / (sa + sb);
+    const double wa = sa * is, wb = sb * is;
+    const double u = fma(wa, ua, wb * ub);
+    const double H = fma(wa, Ha, wb * Hb);
+    const double gm1 = gamma - 1.0;
+    const double c2 = gm1 * fma(-0.5 * u, u, H);
+    const double ic = rsqrt(c2);
+    const double c = c2 * ic;
+    const double hb1 = 0.5 * gm1 * ic * ic;  // b1 / 2
+    const double hb2 = 0.5 * u * u * hb1;    // b2 / 2
+    const double uic = 0.5 * u * ic;
+    const double hb1u = hb1 * u;
+    L[0] = 0.5 * (hb2 + uic);
+    L[1] = -0.5 * (hb1u + 0.5 * ic);
+    L[2] = 0.5 * hb1;
+    L[3] = 0.5 - hb2;
+    L[4] = hb1u;
+    L[5] = -hb1;
+    L[6] = 0.5 * (hb2 - uic);
+    L[7] = -0.5 * (hb1u - 0.5 * ic);
+    L[8] = 0.5 * hb1;
+    rs[0] = u;
+    rs[1] = H;
+    rs[2] = c;
+  }
+
+  __device__ __forceinline__ static void project3(const double* l, const double* f, const double* U, double alpha,
+                                                  double& vp, double& vm) {
+    const double a = fma(l[2], f[2], fma(l[1], f[1], l[0] * f[0]));
+    const double b = fma(l[2], U[2], fma(l[1], U[1], l[0] * U[0]));
+    vp = fma(alpha, b, a);
+    vm = fma(-alpha, b, a);
+  }
+  __device__ __forceinline__ static void project1(double f, double u, double alpha, double& vp, double& vm) {
+    const double hu = 0.5 * u;
+    vp = fma(alpha, hu, 0.5 * f);
+    vm = fma(-alpha, hu, 0.5 * f);
+  }
+
+  __device__ __forceinline__ static double weno(const double* q, double eps, double alpha_R) {
+    constexpr double C1312 = 13.0 / 12.0, C1348 = 13.0 / 48.0;
+    const double d0 = q[1] - q[0], d1 = q[2] - q[1], d2 = q[3] - q[2], d3 = q[4] - q[3], d4 = q[5] - q[4];
+    const double s0 = d1 - d0, s1 = d2 - d1, s2 = d3 - d2, s3 = d4 - d3;
+    // Eqs. (be0_cen)-(be3_cen)
+    const double e0 = s0 + d1;                 // q0 - 3 q1 + 2 q2
+    const double dd = d2 * d2;                 // (q3 - q2)^2, shared by beta_1 and beta_2
+    const double g3 = fma(3.0, s2, -s3);       // 3 q2 - 7 q3 + 5 q4 - q5
+    const double e3 = s3 - d3;                 // 2 q3 - 3 q4 + q5
+    const double b0 = fma(C1312 * s0, s0, e0 * e0);
+    const double b1 = fma(C1312 * s1, s1, dd);
+    const double b2 = fma(C1312 * s2, s2, dd);
+    const double b3 = fma(C1348 * g3, g3, e3 * e3);
+    // Eqs. (tau_5), (tau_6)
+    const double t5b = s2 - s1;                // -q1 + 3 q2 - 3 q3 + q4
+    const double t5a = fma(-2.0, s1, s0) + s2; // q0 - 4 q1 + 6 q2 - 4 q3 + q4
+    const double t6a = fma(-3.0, t5b, s3 - s0);      // fifth difference
+    const double t6b = (s0 + s3) - (s1 + s2);        // q0 - 3 q1 + 2 q2 + 2 q3 - 3 q4 + q5
+    const double tau5 = fma(C1312 * t5a, t5a, t5b * t5b);
+    const double tau6 = fma(C1312 * t6a, t6a, 0.25 * (t6b * t6b));
+    // Eqs. (fh0)-(fh3) in difference form
+    const double fh0 = fma(5.0 / 6.0, d1, fma(-1.0 / 3.0, d0, q[2]));
+    const double fh1 = fma(1.0 / 6.0, d1, fma(1.0 / 3.0, d2, q[2]));
+    const double fh2 = fma(2.0 / 3.0, d2, fma(-1.0 / 6.0, d3, q[2]));
+    const double fh3 = fma(1.0 / 3.0, d4, fma(-5.0 / 6.0, d3, q[3]));
+    // Eq. (tau_we6) and Eq. (gam_we6)
+    const bool theta1 = !(bits(tau6) < bits(tau5));
+    const double tau = theta1 ? tau5 : tau6;
+    const double g0 = theta1 ? 2.0 / 20.0 : 1.0 / 20.0;
+    const double g1 = theta1 ? 12.0 / 20.0 : 9.0 / 20.0;
+    const double g2 = theta1 ? 6.0 / 20.0 : 9.0 / 20.0;
+    const double g3w = theta1 ? 0.0 : 1.0 / 20.0;
+    // Eq. (be_res)
+    const double bmax = nmax(nmax(b0, b1), nmax(b2, b3));
+    const double bmin = nmin(nmin(b0, b1), nmin(b2, b3));
+    const bool restricted = !(bits(fma(alpha_R, bmin, alpha_R * eps)) < bits(bmax));
+    if (restricted) return fma(g3w, fh3, fma(g2, fh2, fma(g1, fh1, g0 * fh0)));
+    // Eq. (om) over the common denominator prod_l (eps + beta_l)
+    const double e0d = eps + b0, e1d = eps + b1, e2d = eps + b2, e3d = eps + b3;
+    const double p01 = e0d * e1d, p23 = e2d * e3d;
+    const double w0 = g0 * (e0d + tau) * (e1d * p23);
+    const double w1 = g1 * (e1d + tau) * (e0d * p23);
+    const double w2 = g2 * (e2d + tau) * (p01 * e3d);
+    const double w3 = g3w * (e3d + tau) * (p01 * e2d);
+    const double num = fma(w3, fh3, fma(w2, fh2, fma(w1, fh1, w0 * fh0)));
+    return num / ((w0 + w1) + (w2 + w3));
+  }
+
+  __device__ __forceinline__ static void backproject(const double* rs, const double* F, double* h) {
+    const double u = rs[0], H = rs[1], c = rs[2];
+    const double s02 = F[0] + F[2], d20 = F[2] - F[0];
+    h[0] = s02 + F[1];
+    h[1] = fma(u, h[0], c * d20);
+    h[2] = fma(H, s02, fma(u * c, d20, 0.5 * u * u * F[1]));
+  }
+
+  __device__ __forceinline__ static double flux_diff(double hp, double hm, double, double inv_dx) {
+    return (hm - hp) * inv_dx;
+  }
+
+  template <int S>
+  __device__ __forceinline__ static double rk(double un, double us, double dt, double L) {
+    if (S == 0) return fma(dt, L, un);
+    if (S == 1) return fma(0.25, fma(dt, L, us), 0.75 * un);
+    return fma(2.0 / 3.0, fma(dt, L, us), (1.0 / 3.0) * un);
+  }
+
+  __device__ __forceinline__ static double cfl_dt(double cfl, double dx, double smax) { return cfl * dx / smax; }
+};
+
+}  // namespace wt

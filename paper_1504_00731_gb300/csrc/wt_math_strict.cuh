@@ -1,0 +1,170 @@
+// Strict arithmetic policy: every formula evaluated as the paper prints it, left to right,
+// one IEEE binary64 operation per +, -, *, / and sqrt.  The translation unit that
+// instantiates it is compiled with -fmad=false, so nothing is contracted into an FMA and
+// the results are those of a literal evaluation, bit for bit.
+#pragma once
+
+#include "wt_device.cuh"
+
+namespace wt {
+
+struct StrictMath {
+  static constexpr bool kStrict = true;
+
+  // ---- scalar fluxes (Eq. (lin_eq), Eq. (bur_eq))
+  __device__ __forceinline__ static double flux_advection(double a, double u) { return a * u; }
+  __device__ __forceinline__ static double flux_burgers(double u) { return 0.5 * u * u; }
+
+  // ---- Euler 1D cell (Sec. 4.2): u = m / rho, p = (gamma - 1)(E - rho u^2 / 2),
+  //      f = (m, p + m u, (E + p) u), H = (E + p) / rho, sqrt(rho) for Roe's average
+  __device__ __forceinline__ static void euler_cell(const double* U, double gamma, double* f, double& u, double& H,
+                                                    double& sr, double& p) {
+    u = U[1] / U[0];
+    p = (gamma - 1.0) * (U[2] - 0.5 * U[0] * u * u);
+    f[0] = U[1];
+    f[1] = p + U[1] * u;
+    f[2] = (U[2] + p) * u;
+    H = (U[2] + p) / U[0];
+    sr = sqrt(U[0]);
+  }
+
+  // |lambda_s| at a cell: (|u - c|, |u|, |u + c|), c = sqrt(gamma p / rho); returns p
+  __device__ __forceinline__ static double euler_speeds(const double* U, double gamma, double* lam) {
+    double u = U[1] / U[0];
+    double p = (gamma - 1.0) * (U[2] - 0.5 * U[0] * u * u);
+    double c = sqrt(gamma * p / U[0]);
+    lam[0] = fabs(u - c);
+    lam[1] = fabs(u);
+    lam[2] = fabs(u + c);
+    return p;
+  }
+
+  // ---- Roe's mean state between two cells and the left eigenvectors L (row-major 3x3)
+  //      of Roe's matrix; rs = (u~, H~, c~) for the right eigenvectors.
+  __device__ __forceinline__ static void roe(double sa, double ua, double Ha, double sb, double ub, double Hb,
+                                             double gamma, double* L, double* rs) {
+    double u = (sa * ua + sb * ub) / (sa + sb);
+    double H = (sa * Ha + sb * Hb) / (sa + sb);
+    double c = sqrt((gamma - 1.0) * (H - 0.5 * u * u));
+    double b1 = (gamma - 1.0) / (c * c);
+    double b2 = 0.5 * u * u * b1;
+    L[0] = 0.5 * (b2 + u / c);
+    L[1] = -0.5 * (b1 * u + 1.0 / c);
+    L[2] = 0.5 * b1;
+    L[3] = 1.0 - b2;
+    L[4] = b1 * u;
+    L[5] = -b1;
+    L[6] = 0.5 * (b2 - u / c);
+    L[7] = -0.5 * (b1 * u - 1.0 / c);
+    L[8] = 0.5 * b1;
+    rs[0] = u;
+    rs[1] = H;
+    rs[2] = c;
+  }
+
+  // ---- Global Lax-Friedrichs splitting of one projected cell (Eq. (flux_split_lf))
+  __device__ __forceinline__ static void project3(const double* l, const double* f, const double* U, double alpha,
+                                                  double& vp, double& vm) {
+    double a = l[0] * f[0];
+    double b = l[0] * U[0];
+    a = a + l[1] * f[1];
+    b = b + l[1] * U[1];
+    a = a + l[2] * f[2];
+    b = b + l[2] * U[2];
+    vp = 0.5 * (a + alpha * b);
+    vm = 0.5 * (a - alpha * b);
+  }
+  __device__ __forceinline__ static void project1(double f, double u, double alpha, double& vp, double& vm) {
+    vp = 0.5 * (f + alpha * u);
+    vm = 0.5 * (f - alpha * u);
+  }
+
+  // ---- WENO-theta interface value, Eqs. (fh0)-(fh3), (be0_cen)-(be3_cen), (be_res),
+  //      (tau_5), (tau_6), (tau_we6), (gam_we6), (om), (fh_nonlinear); q[i] at x_{j-2+i}
+  __device__ __forceinline__ static double weno(const double* q, double eps, double alpha_R) {
+    double fh0 = (2.0 * q[0] - 7.0 * q[1] + 11.0 * q[2]) / 6.0;
+    double fh1 = (-q[1] + 5.0 * q[2] + 2.0 * q[3]) / 6.0;
+    double fh2 = (2.0 * q[2] + 5.0 * q[3] - q[4]) / 6.0;
+    double fh3 = (11.0 * q[3] - 7.0 * q[4] + 2.0 * q[5]) / 6.0;
+    double x, y;
+    x = q[0] - 2.0 * q[1] + q[2];
+    y = q[0] - 3.0 * q[1] + 2.0 * q[2];
+    double b0 = (13.0 / 12.0) * (x * x) + y * y;
+    x = q[1] - 2.0 * q[2] + q[3];
+    y = q[3] - q[2];
+    double b1 = (13.0 / 12.0) * (x * x) + y * y;
+    x = q[2] - 2.0 * q[3] + q[4];
+    y = q[2] - q[3];
+    double b2 = (13.0 / 12.0) * (x * x) + y * y;
+    x = 3.0 * q[2] - 7.0 * q[3] + 5.0 * q[4] - q[5];
+    y = 2.0 * q[3] - 3.0 * q[4] + q[5];
+    double b3 = (13.0 / 48.0) * (x * x) + y * y;
+    x = q[0] - 4.0 * q[1] + 6.0 * q[2] - 4.0 * q[3] + q[4];
+    y = -q[1] + 3.0 * q[2] - 3.0 * q[3] + q[4];
+    double tau5 = (13.0 / 12.0) * (x * x) + y * y;
+    x = -q[0] + 5.0 * q[1] - 10.0 * q[2] + 10.0 * q[3] - 5.0 * q[4] + q[5];
+    y = q[0] - 3.0 * q[1] + 2.0 * q[2] + 2.0 * q[3] - 3.0 * q[4] + q[5];
+    double tau6 = (13.0 / 12.0) * (x * x) + 0.25 * (y * y);
+
+    double bmax = b0, bmin = b0;
+    bmax = (bmax < b1) ? b1 : bmax;
+    bmax = (bmax < b2) ? b2 : bmax;
+    bmax = (bmax < b3) ? b3 : bmax;
+    bmin = (b1 < bmin) ? b1 : bmin;
+    bmin = (b2 < bmin) ? b2 : bmin;
+    bmin = (b3 < bmin) ? b3 : bmin;
+    double ratio = bmax / (eps + bmin);
+    if (ratio <= alpha_R) {
+      b0 = 0.0;
+      b1 = 0.0;
+      b2 = 0.0;
+      b3 = 0.0;
+    }
+    double tau, g0, g1, g2, g3;
+    if (tau6 < tau5) {  // theta = 0
+      tau = tau6;
+      g0 = (1.0 + 0.0) / 20.0;
+      g1 = (3.0 * (3.0 + 0.0)) / 20.0;
+      g2 = (3.0 * (3.0 - 0.0)) / 20.0;
+      g3 = (1.0 - 0.0) / 20.0;
+    } else {  // theta = 1
+      tau = tau5;
+      g0 = (1.0 + 1.0) / 20.0;
+      g1 = (3.0 * (3.0 + 1.0)) / 20.0;
+      g2 = (3.0 * (3.0 - 1.0)) / 20.0;
+      g3 = (1.0 - 1.0) / 20.0;
+    }
+    double a0 = g0 * (1.0 + tau / (eps + b0));
+    double a1 = g1 * (1.0 + tau / (eps + b1));
+    double a2 = g2 * (1.0 + tau / (eps + b2));
+    double a3 = g3 * (1.0 + tau / (eps + b3));
+    double asum = a0 + a1 + a2 + a3;
+    double w0 = a0 / asum, w1 = a1 / asum, w2 = a2 / asum, w3 = a3 / asum;
+    return w0 * fh0 + w1 * fh1 + w2 * fh2 + w3 * fh3;
+  }
+
+  // ---- back-projection h = R (F+ + F-) with R = [r_1 r_2 r_3] of Roe's matrix
+  __device__ __forceinline__ static void backproject(const double* rs, const double* F, double* h) {
+    const double u = rs[0], H = rs[1], c = rs[2];
+    h[0] = 1.0 * F[0] + 1.0 * F[1] + 1.0 * F[2];
+    h[1] = (u - c) * F[0] + u * F[1] + (u + c) * F[2];
+    h[2] = (H - u * c) * F[0] + 0.5 * u * u * F[1] + (H + u * c) * F[2];
+  }
+
+  // ---- Eq. (mod_semi)
+  __device__ __forceinline__ static double flux_diff(double hp, double hm, double dx, double) {
+    return -(hp - hm) / dx;
+  }
+
+  // ---- Eq. (3rd_RK), stage s of uout from u^n, the stage input us and L(us)
+  template <int S>
+  __device__ __forceinline__ static double rk(double un, double us, double dt, double L) {
+    if (S == 0) return un + dt * L;
+    if (S == 1) return 0.75 * un + 0.25 * us + 0.25 * dt * L;
+    return (1.0 / 3.0) * un + (2.0 / 3.0) * us + (2.0 / 3.0) * dt * L;
+  }
+
+  __device__ __forceinline__ static double cfl_dt(double cfl, double dx, double smax) { return cfl * dx / smax; }
+};
+
+}  // namespace wt

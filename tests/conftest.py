@@ -19,3 +19,13 @@ def oracle():
 
     O.lib()
     return O
+
+
+@pytest.fixture(scope="session")
+def wtlib():
+    """The CUDA library, built in-tree if it is missing or stale (nvcc needed, no GPU)."""
+    from paper_1504_00731_gb300 import binding, build
+
+    build.build_library()
+    binding.lib()
+    return binding
