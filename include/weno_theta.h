@@ -164,6 +164,29 @@ int weno_theta_adjoint(const wt_problem* prob, const wt_grid* grid, const double
                        int32_t checkpoint_every, const double* dJ_duT, double* dJ_du0, double* uT, void* ws,
                        size_t ws_bytes, void* stream);
 
+/*
+ * L(u) exactly as weno_theta_rhs computes it, for callers that cannot allocate device
+ * memory and so cannot supply a workspace: a host program with no device allocator of
+ * its own, a plug-in confined to its host application's fixed memory budget, or a
+ * real-time loop in which an allocation would synchronise the device.  The paper has no
+ * counterpart; this is a deployment variant of the RHS evaluation.
+ *
+ * Its scratch (control block and padded state with ghost cells) lives in one array of
+ * WT_NOALLOC_SCRATCH_BYTES of device memory built into the library; every GPU that loads
+ * the library holds that array until the process exits.  The call allocates and frees
+ * nothing.  Sizes whose scratch does not fit (n > 349498 cells for Euler 1D, n > 1048506
+ * for a scalar flux) are rejected with WT_ERR_ARG.  1D fluxes only.
+ *   u  [m][n]  input, device memory
+ *   L  [m][n]  output, device memory on the same GPU
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.  Every call
+ * reuses the same array and each clears what must start at zero; calls whose GPU work
+ * overlaps (other streams or host threads) race on it and must be serialised.
+ * Asynchronous on `stream`.
+ */
+#define WT_NOALLOC_SCRATCH_BYTES (8u << 20)
+int weno_theta_rhs_noalloc(const wt_problem* prob, const wt_grid* grid, const double* u, double* L, void* stream);
+
 /* Message describing the last non-OK status returned on the calling thread. */
 const char* wt_last_error(void);
 

@@ -29,6 +29,7 @@ EXPORTED = (
     "weno_theta_step_batched",
     "wt_adjoint_workspace_bytes",
     "weno_theta_adjoint",
+    "weno_theta_rhs_noalloc",
     "wt_last_error",
 )
 
@@ -103,6 +104,8 @@ def lib():
     L.weno_theta_adjoint.argtypes = [P(WtProblem), P(WtGrid), vp, ctypes.c_double, ctypes.c_int64, ctypes.c_int32,
                                      vp, vp, vp, vp, ctypes.c_size_t, vp]
     L.weno_theta_adjoint.restype = ctypes.c_int
+    L.weno_theta_rhs_noalloc.argtypes = [P(WtProblem), P(WtGrid), vp, vp, vp]
+    L.weno_theta_rhs_noalloc.restype = ctypes.c_int
     L.wt_last_error.argtypes = []
     L.wt_last_error.restype = ctypes.c_char_p
     _lib = L
@@ -208,6 +211,13 @@ def weno_theta_rhs(prob, grid, u, L, ws, stream=None):
     wp, _ = _ptr(ws)
     _check(lib().weno_theta_rhs(ctypes.byref(prob), ctypes.byref(grid), up, Lp, wp, _nbytes(ws),
                                 _stream(stream, u, ws)))
+
+
+def weno_theta_rhs_noalloc(prob, grid, u, L, stream=None):
+    """L(u) with the library's built-in scratch array instead of a caller workspace
+    (for callers that cannot allocate device memory); u and L are device arrays."""
+    _check(lib().weno_theta_rhs_noalloc(ctypes.byref(prob), ctypes.byref(grid), _ptr(u)[0], _ptr(L)[0],
+                                        _stream(stream, u, L)))
 
 
 def weno_theta_step(prob, grid, u, cfl, ws, dt_fixed=0.0, t_final=float("inf"), max_steps=2**62, stream=None):

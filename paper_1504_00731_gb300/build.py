@@ -18,6 +18,7 @@ UNITS = {
     "wt_api.cu": [],
     "wt_kernels_fast.cu": [],
     "wt_kernels_strict.cu": ["-fmad=false"],
+    "wt_noalloc.cu": [],
 }
 
 

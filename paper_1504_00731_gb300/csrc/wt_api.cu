@@ -269,6 +269,8 @@ Ctl make_ctl(double cfl, double dt_fixed, double t_final) {
 
 }  // namespace
 
+int wt::set_last_error(int code, const char* msg) { return fail(code, "%s", msg); }
+
 extern "C" {
 
 const char* wt_last_error(void) { return g_err.c_str(); }

@@ -24,6 +24,9 @@ struct Stage1DArgs {
   Ctl* ctl;
 };
 
+// Records a message for wt_last_error() on the calling thread and returns code.
+int set_last_error(int code, const char* msg);
+
 cudaError_t launch_stage1d_strict(int flux, int stage, int tile, const Stage1DArgs& a, cudaStream_t st);
 cudaError_t launch_stage1d_fast(int flux, int stage, int tile, const Stage1DArgs& a, cudaStream_t st);
 cudaError_t launch_alpha1d_strict(int flux, const double* u, long long n, long long pitch, double gamma, double adv,
