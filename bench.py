@@ -147,7 +147,7 @@ def cpu_baseline(sample_steps=RK_STEPS):
     import oracle as O
 
     U, x, dx = W.euler_c2(N_CELLS, seed=0)
-    P = O.problem(O.FLUX_EULER1D, bc=O.BC_OUTFLOW)
+    P = O.problem(O.FLUX_EULER1D, bc=O.BC_OUTFLOW, alpha_R=W.ALPHA_R_SEEDED)
     O.lib()
     t0 = time.perf_counter()
     _, _, steps = O.run(P, U, dx, cfl=CFL, n_steps=sample_steps)
@@ -155,6 +155,68 @@ def cpu_baseline(sample_steps=RK_STEPS):
     return {"value": N_CELLS * steps / el, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
             "sample": f"serial C++ oracle (-O2, no FMA contraction), seed-0 workload, {steps} of the {RK_STEPS} RK3 "
                       f"steps ({el:.2f} s)", "seconds": el}
+
+
+def batched_measure(B, dev, steps=20, plain_sample=64):
+    """The batched workload (4096 independent 1D Euler problems, lengths log-uniform in
+    [256, 65536], mixed periodic/outflow, per-problem CFL step) advanced through the batched
+    entry point, against per-problem calls of the single-problem entry point on a seeded
+    sample of the same problems.  Both are timed over `steps` RK steps (the workload runs
+    200; throughput per step does not depend on the count)."""
+    import torch
+
+    batch = W.euler_batch(4096, seed=0)
+    prob = B.problem(B.WT_FLUX_EULER1D, mode=B.WT_MODE_FAST, alpha_R=W.ALPHA_R_SEEDED)
+    segs = []
+    for p in range(len(batch.lengths)):
+        s = B.WtSegment()
+        s.offset, s.n = int(batch.offsets[p]), int(batch.lengths[p])
+        s.lo, s.hi = -5.0, 5.0
+        s.bc_lo = s.bc_hi = int(batch.bc[p])
+        segs.append(s)
+    total = int(batch.u.shape[1])
+    ws = B.alloc_workspace(B.workspace_bytes(prob, None, total, len(segs)), dev)
+    u0 = torch.from_numpy(batch.u).to(dev)
+    u = u0.clone()
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(3):  # autotune on first call, then warm
+        u.copy_(u0)
+        B.weno_theta_step_batched(prob, segs, u, total, 0.5, 1, ws)
+    u.copy_(u0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    B.weno_theta_step_batched(prob, segs, u, total, 0.5, steps, ws)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_b = e0.elapsed_time(e1) * 1e-3
+    finite = bool(torch.isfinite(u).all())
+    rng = np.random.default_rng(0)
+    sample = rng.choice(len(segs), plain_sample, replace=False)
+    t_p, cells_p = 0.0, 0
+    for p in sample:
+        o, n = int(batch.offsets[p]), int(batch.lengths[p])
+        pb = B.problem(B.WT_FLUX_EULER1D, bc=int(batch.bc[p]), mode=B.WT_MODE_FAST, alpha_R=W.ALPHA_R_SEEDED)
+        g = B.grid_1d(n, -5.0, 5.0)
+        w = B.alloc_workspace(B.workspace_bytes(pb, g), dev)
+        us = u0[:, o:o + n].contiguous()
+        for _ in range(3):
+            B.weno_theta_step(pb, g, us, 0.5, w, max_steps=1)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        B.weno_theta_step(pb, g, us, 0.5, w, max_steps=steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_p += e0.elapsed_time(e1) * 1e-3
+        cells_p += n
+    v_b = total * steps / t_b
+    v_p = cells_p * steps / t_p
+    small = [p for p in sample if batch.lengths[p] <= 2048]
+    return {"value": v_b, "unit": "cell-updates/s", "plain_value": v_p, "batched_over_plain": v_b / v_p,
+            "problems": len(segs), "cells": total, "rk_steps_timed": steps, "finite": finite,
+            "plain_sample": f"{plain_sample} seeded problems through weno_theta_step one at a time",
+            "roofline_frac_alu": v_b * FLOPS_PER_CELL_UPDATE / 1e9 / FP64_PEAK_GFLOPS,
+            "workload": "4096 x 1D Euler, N log-uniform in [256, 65536], mixed periodic/outflow, CFL 0.5"}
 
 
 def run_reference(args):
@@ -166,7 +228,7 @@ def run_reference(args):
     O.lib()
     sample = 100  # RK steps per benchmark step: a bounded sample of the 2000-step run
     U, x, dx = W.euler_c2(N_CELLS, seed=0)
-    P = O.problem(O.FLUX_EULER1D, bc=O.BC_OUTFLOW)
+    P = O.problem(O.FLUX_EULER1D, bc=O.BC_OUTFLOW, alpha_R=W.ALPHA_R_SEEDED)
     for _ in range(args.warmup):
         O.run(P, U, dx, cfl=CFL, n_steps=sample)
     times = []
@@ -210,7 +272,7 @@ def run_ours(args):
     B.lib()
 
     U0, x, dx = W.euler_c2(N_CELLS, seed=rank)
-    prob = B.problem(B.WT_FLUX_EULER1D, bc=B.WT_BC_OUTFLOW, mode=B.WT_MODE_FAST)
+    prob = B.problem(B.WT_FLUX_EULER1D, bc=B.WT_BC_OUTFLOW, mode=B.WT_MODE_FAST, alpha_R=W.ALPHA_R_SEEDED)
     grid = B.grid_1d(N_CELLS, -5.0, 5.0)
     ws = B.alloc_workspace(B.workspace_bytes(prob, grid), dev)
     u_src = torch.from_numpy(U0).to(dev)
@@ -287,7 +349,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": N_CELLS, "rk_steps": RK_STEPS, "m": M, "cfl": CFL,
-                       "bc": "outflow", "mode": "fast", "alpha_R": 50.0, "eps": 1e-10,
+                       "bc": "outflow", "mode": "fast", "alpha_R": W.ALPHA_R_SEEDED, "eps": 1e-10,
                        "l2": "flushed between timed runs (256 MiB write, untimed)",
                        "parallelism": f"replicas: one seeded problem per GPU ({world})"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
@@ -302,6 +364,8 @@ def run_ours(args):
             "clocks": clk.summary(),
             "wall_s_timed_region": wall,
         }
+        if world == 1 and not args.no_extras:
+            line["batched"] = batched_measure(B, dev)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)
@@ -316,6 +380,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched and adjoint measurements")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -41,7 +41,9 @@ typedef enum {
   WT_ERR_ARG = -1,          /* invalid argument (sizes, pointers, enums, alignment) */
   WT_ERR_UNSUPPORTED = -2,  /* valid but not implemented (e.g. reflective scalar) */
   WT_ERR_CUDA = -3,         /* a CUDA runtime call failed */
-  WT_ERR_NONPHYSICAL = -4,  /* rho <= 0, p <= 0 or a NaN met during integration */
+  WT_ERR_NONPHYSICAL = -4,  /* the state became non-finite (NaN or Inf); a negative pressure or
+                             * density in an intermediate RK stage is not an error: the scheme
+                             * has no positivity limiter and integration continues through it */
   WT_ERR_TIMEOUT = -5,      /* a bounded device-side wait gave up */
   WT_ERR_WORKSPACE = -6     /* workspace missing, misaligned or too small */
 } wt_status;

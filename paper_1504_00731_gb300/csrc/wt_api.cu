@@ -4,6 +4,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -267,6 +268,140 @@ Ctl make_ctl(double cfl, double dt_fixed, double t_final) {
   return h;
 }
 
+
+// --- batched stepping -------------------------------------------------------------------
+
+int tile_candidates(int flux, int* out) {
+  if (flux == WT_FLUX_EULER1D) {
+    out[0] = 31;
+    out[1] = 63;
+    out[2] = 127;
+    return 3;
+  }
+  out[0] = 63;
+  out[1] = 127;
+  return 2;
+}
+
+struct BatchLayout {
+  size_t ctl, segs, tiles, un, u1, u2, st_u, st_t, total;
+  long long pitch;
+  long long max_tiles;
+};
+
+BatchLayout layout_batched(int m, int nprob, long long pitch, long long max_tiles, long long total_cells) {
+  BatchLayout L;
+  L.pitch = pitch;
+  L.max_tiles = max_tiles;
+  const size_t plane = (size_t)m * pitch * sizeof(double);
+  size_t o = 0;
+  L.ctl = o;
+  o = align_up(o + sizeof(Ctl) * (size_t)nprob);
+  L.segs = o;
+  o = align_up(o + sizeof(BatchSeg) * (size_t)nprob);
+  L.tiles = o;
+  o = align_up(o + sizeof(int2) * (size_t)max_tiles);
+  L.un = o;
+  o = align_up(o + plane);
+  L.u1 = o;
+  o = align_up(o + plane);
+  L.u2 = o;
+  o = align_up(o + plane);
+  L.st_u = o;
+  o = align_up(o + sizeof(double) * (size_t)m * total_cells);
+  L.st_t = o;
+  o = align_up(o + sizeof(double) * (size_t)nprob);
+  L.total = o;
+  return L;
+}
+
+// upper bounds used by wt_workspace_bytes when only the batch totals are known
+long long batched_pitch_bound(long long cells, int nprob) { return ((cells + 8LL * nprob + 31) / 32) * 32; }
+long long batched_tiles_bound(long long cells, int nprob) { return cells / 31 + nprob; }
+
+std::vector<int2> make_tiles(const std::vector<BatchSeg>& segs, int T) {
+  std::vector<int2> t;
+  // largest problems first, so the tail of the persistent loop is made of short work
+  std::vector<int> order(segs.size());
+  for (size_t i = 0; i < segs.size(); ++i) order[i] = (int)i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return segs[a].n > segs[b].n; });
+  for (int p : order) {
+    const long long nt = (segs[p].n + T - 1) / T;
+    for (long long k = 0; k < nt; ++k) t.push_back(make_int2(p, (int)k));
+  }
+  return t;
+}
+
+struct BatchGraph {
+  BatchArgs a[3];
+  int flux, mode, tile, grid, device;
+  cudaGraphExec_t exec;
+};
+std::vector<BatchGraph> g_bgraphs;
+struct TuneEntry {
+  int flux, mode, nprob, device;
+  long long total, pitch;
+  int tile;
+};
+std::vector<TuneEntry> g_tuned;
+
+int batched_grid_size(const wt_problem* p, int tile, long long ntiles, int device) {
+  int occ = p->mode == WT_MODE_STRICT ? stage1d_batched_occupancy_strict(p->flux, tile)
+                                      : stage1d_batched_occupancy_fast(p->flux, tile);
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  long long g = (long long)(occ > 0 ? occ : 1) * (sms > 0 ? sms : 1);
+  if (g > ntiles) g = ntiles;
+  return (int)(g < 1 ? 1 : g);
+}
+
+cudaError_t launch_batched_stage(const wt_problem* p, int stage, int tile, const BatchArgs& b, int grid,
+                                 cudaStream_t st) {
+  return p->mode == WT_MODE_STRICT ? launch_stage1d_batched_strict(p->flux, stage, tile, b, grid, st)
+                                   : launch_stage1d_batched_fast(p->flux, stage, tile, b, grid, st);
+}
+
+int get_batched_graph(const wt_problem* p, int device, int tile, int grid, const BatchArgs a[3], cudaGraphExec_t* out) {
+  std::lock_guard<std::mutex> lk(g_graph_mu);
+  for (auto& e : g_bgraphs) {
+    if (e.device == device && e.flux == p->flux && e.mode == p->mode && e.tile == tile && e.grid == grid &&
+        !memcmp(&e.a[0], &a[0], sizeof(BatchArgs)) && !memcmp(&e.a[1], &a[1], sizeof(BatchArgs)) &&
+        !memcmp(&e.a[2], &a[2], sizeof(BatchArgs))) {
+      *out = e.exec;
+      return WT_OK;
+    }
+  }
+  if (device < 0 || device >= 64) return fail(WT_ERR_CUDA, "device index %d out of range", device);
+  cudaStream_t& cs = g_capture_stream[device];
+  if (!cs) WT_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  WT_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  cudaError_t le = cudaSuccess;
+  for (int s = 0; s < 3 && le == cudaSuccess; ++s) le = launch_batched_stage(p, s, tile, a[s], grid, cs);
+  cudaGraph_t graph = nullptr;
+  cudaError_t ee = cudaStreamEndCapture(cs, &graph);
+  if (le != cudaSuccess) return fail(WT_ERR_CUDA, "batched stage launch during capture: %s", cudaGetErrorString(le));
+  if (ee != cudaSuccess) return fail(WT_ERR_CUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(ee));
+  cudaGraphExec_t exec = nullptr;
+  cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ie != cudaSuccess) return fail(WT_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(ie));
+  if (g_bgraphs.size() >= 8) {
+    cudaGraphExecDestroy(g_bgraphs.front().exec);
+    g_bgraphs.erase(g_bgraphs.begin());
+  }
+  BatchGraph e;
+  memcpy(e.a, a, sizeof e.a);
+  e.flux = p->flux;
+  e.mode = p->mode;
+  e.tile = tile;
+  e.grid = grid;
+  e.device = device;
+  e.exec = exec;
+  g_bgraphs.push_back(e);
+  *out = exec;
+  return WT_OK;
+}
+
 }  // namespace
 
 int wt::set_last_error(int code, const char* msg) { return fail(code, "%s", msg); }
@@ -281,10 +416,17 @@ size_t wt_workspace_bytes(const wt_problem* prob, const wt_grid* grid, int64_t b
     if (check_grid_1d(prob, grid) != WT_OK) return 0;
     return layout_1d(prob->m, grid->n[0]).total;
   }
-  (void)batch_cells;
-  (void)nprob;
-  fail(WT_ERR_UNSUPPORTED, "batched workspace is not available in this build");
-  return 0;
+  if (prob->flux == WT_FLUX_EULER2D) {
+    fail(WT_ERR_UNSUPPORTED, "batched stepping supports the 1D fluxes only");
+    return 0;
+  }
+  if (batch_cells < 3 || nprob < 1 || nprob > 65535) {
+    fail(WT_ERR_ARG, "need batch_cells >= 3 and 1 <= nprob <= 65535");
+    return 0;
+  }
+  return layout_batched(prob->m, nprob, batched_pitch_bound(batch_cells, nprob),
+                        batched_tiles_bound(batch_cells, nprob), batch_cells)
+      .total;
 }
 
 int weno_theta_rhs(const wt_problem* prob, const wt_grid* grid, const double* u, double* L, void* ws, size_t ws_bytes,
@@ -412,9 +554,191 @@ int weno_theta_step(const wt_problem* prob, const wt_grid* grid, double* u, doub
 int weno_theta_step_batched(const wt_problem* prob, const wt_segment* segs, int32_t nprob, double* u_packed,
                             int64_t total, double cfl, int64_t n_steps, double* t_per_problem, void* ws,
                             size_t ws_bytes, void* stream) {
-  (void)prob; (void)segs; (void)nprob; (void)u_packed; (void)total; (void)cfl; (void)n_steps; (void)t_per_problem;
-  (void)ws; (void)ws_bytes; (void)stream;
-  return fail(WT_ERR_UNSUPPORTED, "batched stepping is not available in this build");
+  int rc;
+  if ((rc = check_problem(prob)) != WT_OK) return rc;
+  if (prob->flux == WT_FLUX_EULER2D) return fail(WT_ERR_UNSUPPORTED, "batched stepping supports the 1D fluxes only");
+  if (!segs || !u_packed) return fail(WT_ERR_ARG, "segs and u_packed must not be NULL");
+  if (nprob < 1 || nprob > 65535) return fail(WT_ERR_ARG, "nprob = %d outside 1..65535", nprob);
+  if (total < 3) return fail(WT_ERR_ARG, "total must be >= 3");
+  if (!(cfl > 0.0) || !std::isfinite(cfl)) return fail(WT_ERR_ARG, "need cfl > 0");
+  if (n_steps < 0) return fail(WT_ERR_ARG, "n_steps must be >= 0");
+  const int m = prob->m;
+  // segments: validate, order by offset to reject overlaps, lay out the padded planes
+  std::vector<int> order(nprob);
+  for (int i = 0; i < nprob; ++i) order[i] = i;
+  std::sort(order.begin(), order.end(), [&](int a, int b) { return segs[a].offset < segs[b].offset; });
+  for (int k = 0; k < nprob; ++k) {
+    const wt_segment& sg = segs[order[k]];
+    if (sg.n < G) return fail(WT_ERR_ARG, "segment %d: n = %lld below 3", order[k], (long long)sg.n);
+    if (sg.offset < 0 || sg.offset + sg.n > total) return fail(WT_ERR_ARG, "segment %d outside [0, total)", order[k]);
+    if (k > 0) {
+      const wt_segment& pv = segs[order[k - 1]];
+      if (pv.offset + pv.n > sg.offset) return fail(WT_ERR_ARG, "segments %d and %d overlap", order[k - 1], order[k]);
+    }
+    if (!(sg.hi > sg.lo)) return fail(WT_ERR_ARG, "segment %d: need lo < hi", order[k]);
+    if (!bc_ok(sg.bc_lo) || !bc_ok(sg.bc_hi)) return fail(WT_ERR_ARG, "segment %d: unknown boundary", order[k]);
+    if ((sg.bc_lo == WT_BC_PERIODIC) != (sg.bc_hi == WT_BC_PERIODIC))
+      return fail(WT_ERR_ARG, "segment %d: periodic at one end only", order[k]);
+    if (m == 1 && (sg.bc_lo == WT_BC_REFLECTIVE || sg.bc_hi == WT_BC_REFLECTIVE))
+      return fail(WT_ERR_UNSUPPORTED, "reflective boundaries are defined for the Euler equations only");
+  }
+  std::vector<BatchSeg> hs(nprob);
+  long long poff = 0, maxn = 0, cells = 0;
+  for (int p = 0; p < nprob; ++p) {
+    const wt_segment& sg = segs[p];
+    hs[p].poff = poff;
+    hs[p].uoff = sg.offset;
+    hs[p].n = sg.n;
+    hs[p].dx = (sg.hi - sg.lo) / (double)sg.n;
+    hs[p].inv_dx = 1.0 / hs[p].dx;
+    hs[p].bc_lo = sg.bc_lo;
+    hs[p].bc_hi = sg.bc_hi;
+    poff += ((sg.n + 2 * G + 1) / 2) * 2;  // even: every problem starts 16-byte aligned
+    maxn = sg.n > maxn ? sg.n : maxn;
+    cells += sg.n;
+  }
+  const long long pitch = ((poff + 31) / 32) * 32;
+  int cand[3];
+  const int ncand = tile_candidates(prob->flux, cand);
+  long long max_tiles = 0;
+  for (int p = 0; p < nprob; ++p) max_tiles += (hs[p].n + cand[0] - 1) / cand[0];
+  const BatchLayout lay = layout_batched(m, nprob, pitch, max_tiles, total);
+  int dev;
+  if ((rc = check_ws(ws, ws_bytes, lay.total, &dev)) != WT_OK) return rc;
+  DeviceGuard guard;
+  if ((rc = guard.enter(dev)) != WT_OK) return rc;
+  bool u_dev, t_dev = false;
+  int d_u, d_t;
+  pointer_info(u_packed, &u_dev, &d_u);
+  if (t_per_problem) pointer_info(t_per_problem, &t_dev, &d_t);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char* w = static_cast<char*>(ws);
+  Ctl* ctl = reinterpret_cast<Ctl*>(w + lay.ctl);
+  BatchSeg* dsegs = reinterpret_cast<BatchSeg*>(w + lay.segs);
+  int2* dtiles = reinterpret_cast<int2*>(w + lay.tiles);
+  double* Un = reinterpret_cast<double*>(w + lay.un);
+  double* U1 = reinterpret_cast<double*>(w + lay.u1);
+  double* U2 = reinterpret_cast<double*>(w + lay.u2);
+  double* st_u = reinterpret_cast<double*>(w + lay.st_u);
+  double* st_t = reinterpret_cast<double*>(w + lay.st_t);
+
+  std::vector<Ctl> hctl(nprob, make_ctl(cfl, 0.0, INFINITY));
+  WT_CUDA(cudaMemcpyAsync(dsegs, hs.data(), sizeof(BatchSeg) * nprob, cudaMemcpyHostToDevice, st));
+  const double* src = u_packed;
+  if (!u_dev) {
+    WT_CUDA(cudaMemcpyAsync(st_u, u_packed, sizeof(double) * m * total, cudaMemcpyHostToDevice, st));
+    src = st_u;
+  }
+  WT_CUDA(launch_pack1d_batched(src, total, Un, pitch, dsegs, nprob, maxn, m, 1, st));
+  auto init_ctl = [&]() -> int {
+    WT_CUDA(cudaMemcpyAsync(ctl, hctl.data(), sizeof(Ctl) * nprob, cudaMemcpyHostToDevice, st));
+    WT_CUDA(prob->mode == WT_MODE_STRICT
+                ? launch_alpha1d_batched_strict(prob->flux, Un, pitch, dsegs, nprob, maxn, prob->gamma,
+                                                prob->adv_speed, ctl, st)
+                : launch_alpha1d_batched_fast(prob->flux, Un, pitch, dsegs, nprob, maxn, prob->gamma,
+                                              prob->adv_speed, ctl, st));
+    return WT_OK;
+  };
+  if ((rc = init_ctl()) != WT_OK) return rc;
+
+  auto args_for = [&](int ntiles) {
+    BatchArgs b;
+    memset(&b, 0, sizeof b);
+    b.pitch = pitch;
+    b.segs = dsegs;
+    b.ctl = ctl;
+    b.tiles = dtiles;
+    b.ntiles = ntiles;
+    b.gamma = prob->gamma;
+    b.adv_speed = prob->adv_speed;
+    b.eps = prob->eps;
+    b.alpha_R = prob->alpha_R;
+    return b;
+  };
+
+  // ---- tile size: autotuned once per batch shape (timed RK stage 1 per candidate)
+  int tile = -1;
+  {
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    for (auto& e : g_tuned)
+      if (e.flux == prob->flux && e.mode == prob->mode && e.nprob == nprob && e.device == dev && e.total == total &&
+          e.pitch == pitch)
+        tile = e.tile;
+  }
+  if (tile < 0 && n_steps > 0) {
+    cudaEvent_t e0, e1;
+    WT_CUDA(cudaEventCreate(&e0));
+    WT_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    for (int ci = 0; ci < ncand; ++ci) {
+      std::vector<int2> tl = make_tiles(hs, cand[ci]);
+      WT_CUDA(cudaMemcpyAsync(dtiles, tl.data(), sizeof(int2) * tl.size(), cudaMemcpyHostToDevice, st));
+      BatchArgs b = args_for((int)tl.size());
+      b.uin = Un;
+      b.uout = U1;
+      const int grid = batched_grid_size(prob, cand[ci], (long long)tl.size(), dev);
+      WT_CUDA(launch_batched_stage(prob, STAGE_RK1, cand[ci], b, grid, st));
+      WT_CUDA(cudaEventRecord(e0, st));
+      for (int r = 0; r < 2; ++r) WT_CUDA(launch_batched_stage(prob, STAGE_RK1, cand[ci], b, grid, st));
+      WT_CUDA(cudaEventRecord(e1, st));
+      WT_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      WT_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) {
+        best = ms;
+        tile = cand[ci];
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    {
+      std::lock_guard<std::mutex> lk(g_graph_mu);
+      g_tuned.push_back(TuneEntry{prob->flux, prob->mode, nprob, dev, total, pitch, tile});
+    }
+    if ((rc = init_ctl()) != WT_OK) return rc;  // the trial launches touched the alpha slots
+  }
+  if (tile < 0) tile = cand[ncand - 1];
+
+  std::vector<int2> tl = make_tiles(hs, tile);
+  WT_CUDA(cudaMemcpyAsync(dtiles, tl.data(), sizeof(int2) * tl.size(), cudaMemcpyHostToDevice, st));
+  const int grid = batched_grid_size(prob, tile, (long long)tl.size(), dev);
+  BatchArgs a[3];
+  for (int s2 = 0; s2 < 3; ++s2) a[s2] = args_for((int)tl.size());
+  a[0].uin = Un;
+  a[0].uout = U1;
+  a[1].uin = U1;
+  a[1].un = Un;
+  a[1].uout = U2;
+  a[2].uin = U2;
+  a[2].un = Un;
+  a[2].uout = Un;
+  if (n_steps > 0) {
+    cudaGraphExec_t exec;
+    if ((rc = get_batched_graph(prob, dev, tile, grid, a, &exec)) != WT_OK) return rc;
+    for (int64_t i = 0; i < n_steps; ++i) WT_CUDA(cudaGraphLaunch(exec, st));
+  }
+  std::vector<Ctl> back(nprob);
+  WT_CUDA(cudaMemcpyAsync(back.data(), ctl, sizeof(Ctl) * nprob, cudaMemcpyDeviceToHost, st));
+  WT_CUDA(cudaStreamSynchronize(st));
+  for (int p = 0; p < nprob; ++p)
+    if (back[p].status != 0)
+      return fail(back[p].status, "problem %d: device reported status %d after %lld steps", p, back[p].status,
+                  back[p].steps);
+  if (u_dev) {
+    WT_CUDA(launch_unpack1d_batched(Un, pitch, u_packed, total, dsegs, nprob, maxn, m, st));
+  } else {
+    WT_CUDA(launch_unpack1d_batched(Un, pitch, st_u, total, dsegs, nprob, maxn, m, st));
+    WT_CUDA(cudaMemcpyAsync(u_packed, st_u, sizeof(double) * m * total, cudaMemcpyDeviceToHost, st));
+  }
+  if (t_per_problem) {
+    if (t_dev) {
+      WT_CUDA(launch_gather_t(ctl, nprob, t_per_problem, st));
+    } else {
+      for (int p = 0; p < nprob; ++p) t_per_problem[p] = back[p].t;
+    }
+  }
+  WT_CUDA(cudaStreamSynchronize(st));
+  return WT_OK;
 }
 
 size_t wt_adjoint_workspace_bytes(const wt_problem* prob, const wt_grid* grid, int64_t n_steps,

@@ -34,6 +34,11 @@ __device__ __forceinline__ void flag_error(Ctl* ctl, int code) {
   if (ctl) atomicCAS(&ctl->status, 0, code);
 }
 
+// The state must stay finite.  Negative pressure (or density) in an intermediate RK stage
+// is not an error: the scheme has no positivity limiter and a literal evaluation carries
+// on through it (the sound speed there is NaN and drops out of the alpha maxima).
+__device__ __forceinline__ bool finite3(const double* U) { return isfinite(U[0]) && isfinite(U[1]) && isfinite(U[2]); }
+
 // ---------------------------------------------------------------------------------------
 // Bulk copies global -> shared (cp.async.bulk, completion on an mbarrier)
 // ---------------------------------------------------------------------------------------

@@ -62,8 +62,8 @@ __global__ void __launch_bounds__(256) alpha1d_kernel(const double* __restrict__
     if (FLUX == WT_FLUX_EULER1D) {
       double U[3] = {u[j + G], u[pitch + j + G], u[2 * pitch + j + G]};
       double lam[3];
-      double p = MATH::euler_speeds(U, gamma, lam);
-      if (!(U[0] > 0.0) || !(p > 0.0)) flag_error(ctl, WT_ERR_NONPHYSICAL);
+      MATH::euler_speeds(U, gamma, lam);
+      if (!finite3(U)) flag_error(ctl, WT_ERR_NONPHYSICAL);
 #pragma unroll
       for (int s = 0; s < M; ++s) v[s] = (v[s] < lam[s]) ? lam[s] : v[s];
     } else {
@@ -76,6 +76,38 @@ __global__ void __launch_bounds__(256) alpha1d_kernel(const double* __restrict__
   block_max_atomic<M>(v, red, ctl->amax[slot]);
 }
 
+// alpha_s of every problem of a batch: blockIdx.y is the problem
+template <class MATH, int FLUX>
+__global__ void __launch_bounds__(256) alpha1d_batched_kernel(const double* __restrict__ u, long long pitch,
+                                                              const BatchSeg* __restrict__ segs, double gamma,
+                                                              double adv, Ctl* ctl) {
+  constexpr int M = FluxM<FLUX>::m;
+  __shared__ double red[4 * 32];
+  const BatchSeg sg = segs[blockIdx.y];
+  Ctl* c = ctl + blockIdx.y;
+  const double* up = u + sg.poff;
+  double v[M];
+#pragma unroll
+  for (int s = 0; s < M; ++s) v[s] = 0.0;
+  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < sg.n;
+       j += (long long)gridDim.x * blockDim.x) {
+    if (FLUX == WT_FLUX_EULER1D) {
+      double U[3] = {up[j + G], up[pitch + j + G], up[2 * pitch + j + G]};
+      double lam[3];
+      MATH::euler_speeds(U, gamma, lam);
+      if (!finite3(U)) flag_error(c, WT_ERR_NONPHYSICAL);
+#pragma unroll
+      for (int s = 0; s < M; ++s) v[s] = (v[s] < lam[s]) ? lam[s] : v[s];
+    } else {
+      double x = up[j + G];
+      double lam = (FLUX == WT_FLUX_ADVECTION) ? fabs(adv) : fabs(x);
+      if (!isfinite(x)) flag_error(c, WT_ERR_NONPHYSICAL);
+      v[0] = (v[0] < lam) ? lam : v[0];
+    }
+  }
+  block_max_atomic<M>(v, red, c->amax[0]);
+}
+
 // ---------------------------------------------------------------------------------------
 // Fused RHS + RK stage (1D).  One CTA per tile of T cells.
 //   A  bulk-copy the stage input (and u^n for stages 2, 3) over cells j0-3 .. j0+T+2
@@ -86,11 +118,11 @@ __global__ void __launch_bounds__(256) alpha1d_kernel(const double* __restrict__
 //   E  per cell: flux difference, RK combine, ghost images, wave speeds of the new state
 // ---------------------------------------------------------------------------------------
 template <class MATH, int FLUX, int STAGE, int T>
-__global__ void __launch_bounds__(Tile1D<T, FluxM<FLUX>::m>::NT) stage1d_kernel(const Stage1DArgs a) {
+__device__ __forceinline__ bool stage1d_tile(const Stage1DArgs& a, const long long j0, const bool first_tile, double* sm,
+                                             uint32_t& phase) {
   constexpr int M = FluxM<FLUX>::m;
   using TL = Tile1D<T, M>;
   constexpr int W = TL::W, NI = TL::NI, NT = TL::NT;
-  extern __shared__ __align__(16) double sm[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + TL::kBar);
   double* s_uin = sm + TL::kUin;
   double* s_un = sm + TL::kUn;
@@ -107,24 +139,22 @@ __global__ void __launch_bounds__(Tile1D<T, FluxM<FLUX>::m>::NT) stage1d_kernel(
   const int tid = threadIdx.x;
   Ctl* ctl = a.ctl;
   const long long n = a.n;
-  const long long j0 = (long long)blockIdx.x * T;
-  if (j0 >= n) return;
+  if (j0 >= n) return true;
   const int Tc = (int)((n - j0 < T) ? (n - j0) : T);
   const int ni = Tc + 1;
-
   // ---- step control: is this step active, and its dt
   double dt = 0.0;
   if (STAGE != STAGE_RHS) {
     if (STAGE == STAGE_RK1) {
       const bool act = (ctl->status == 0) && (ctl->t < ctl->t_final);
       if (!act) {
-        if (blockIdx.x == 0 && tid == 0) ctl->active = 0;
-        return;
+        if (first_tile && tid == 0) ctl->active = 0;
+        return true;
       }
     } else if (ctl->active == 0) {
-      return;
+      return true;
     }
-    if (blockIdx.x == 0 && tid < 8) ctl->amax[(STAGE + 2) % 3][tid] = 0ull;
+    if (first_tile && tid < 8) ctl->amax[(STAGE + 2) % 3][tid] = 0ull;
   }
   const int slot_in = (STAGE == STAGE_RHS) ? 0 : STAGE;
   double alpha[M];
@@ -135,7 +165,7 @@ __global__ void __launch_bounds__(Tile1D<T, FluxM<FLUX>::m>::NT) stage1d_kernel(
     dt = ctl->dt_fixed > 0.0 ? ctl->dt_fixed : MATH::cfl_dt(ctl->cfl, a.dx, smax);
     const double rem = ctl->t_final - ctl->t;
     if (rem < dt) dt = rem;
-    if (blockIdx.x == 0 && tid == 0) {
+    if (first_tile && tid == 0) {
       ctl->dt = dt;
       ctl->active = 1;
     }
@@ -149,8 +179,6 @@ __global__ void __launch_bounds__(Tile1D<T, FluxM<FLUX>::m>::NT) stage1d_kernel(
   const int cells = Tc + 2 * G;
   const int len = (off + cells + 1) & ~1;
   constexpr bool kNeedUn = (STAGE == STAGE_RK2 || STAGE == STAGE_RK3);
-  if (tid == 0) mbar_init(bar, 1);
-  __syncthreads();
   if (tid == 0) {
     const uint32_t bytes = (uint32_t)len * 8u;
     mbar_arrive_expect_tx(bar, bytes * (kNeedUn ? 2 * M : M));
@@ -161,12 +189,13 @@ __global__ void __launch_bounds__(Tile1D<T, FluxM<FLUX>::m>::NT) stage1d_kernel(
       for (int c = 0; c < M; ++c) bulk_g2s(s_un + c * W, a.un + c * a.pitch + s0, bytes, bar);
     }
   }
-  const bool ok = mbar_wait_bounded(bar, 0);
+  const bool ok = mbar_wait_bounded(bar, phase);
   if (__syncthreads_or(ok ? 0 : 1)) {
     if (tid == 0) flag_error(ctl, WT_ERR_TIMEOUT);
-    mbar_wait_bounded(bar, 0);
-    return;
+    mbar_wait_bounded(bar, phase);
+    return false;
   }
+  phase ^= 1u;
 
   // ---- B: per-cell quantities
   for (int k = tid; k < cells; k += NT) {
@@ -174,7 +203,7 @@ __global__ void __launch_bounds__(Tile1D<T, FluxM<FLUX>::m>::NT) stage1d_kernel(
       double U[3] = {s_uin[off + k], s_uin[W + off + k], s_uin[2 * W + off + k]};
       double f[3], u, H, sr, p;
       MATH::euler_cell(U, a.gamma, f, u, H, sr, p);
-      if (!(U[0] > 0.0) || !(p > 0.0)) flag_error(ctl, WT_ERR_NONPHYSICAL);
+      if (!finite3(U)) flag_error(ctl, WT_ERR_NONPHYSICAL);
       s_f[k] = f[0];
       s_f[W + k] = f[1];
       s_f[2 * W + k] = f[2];
@@ -283,8 +312,8 @@ __global__ void __launch_bounds__(Tile1D<T, FluxM<FLUX>::m>::NT) stage1d_kernel(
       }
       if (FLUX == WT_FLUX_EULER1D) {
         double lam[3];
-        const double p = MATH::euler_speeds(uo, a.gamma, lam);
-        if (!(uo[0] > 0.0) || !(p > 0.0)) flag_error(ctl, WT_ERR_NONPHYSICAL);
+        MATH::euler_speeds(uo, a.gamma, lam);
+        if (!finite3(uo)) flag_error(ctl, WT_ERR_NONPHYSICAL);
 #pragma unroll
         for (int s = 0; s < M; ++s) vmax[s] = (vmax[s] < lam[s]) ? lam[s] : vmax[s];
       } else {
@@ -296,10 +325,56 @@ __global__ void __launch_bounds__(Tile1D<T, FluxM<FLUX>::m>::NT) stage1d_kernel(
   }
   if (STAGE != STAGE_RHS) {
     block_max_atomic<M>(vmax, s_red, ctl->amax[(STAGE + 1) % 3]);
-    if (STAGE == STAGE_RK3 && blockIdx.x == 0 && tid == 0) {
+    if (STAGE == STAGE_RK3 && first_tile && tid == 0) {
       ctl->t = ctl->t + dt;
       ctl->steps = ctl->steps + 1;
     }
+  }
+  return true;
+}
+
+template <class MATH, int FLUX, int STAGE, int T>
+__global__ void __launch_bounds__(Tile1D<T, FluxM<FLUX>::m>::NT) stage1d_kernel(const Stage1DArgs a) {
+  using TL = Tile1D<T, FluxM<FLUX>::m>;
+  extern __shared__ __align__(16) double sm[];
+  if (threadIdx.x == 0) mbar_init(reinterpret_cast<uint64_t*>(sm + TL::kBar), 1);
+  __syncthreads();
+  uint32_t phase = 0;
+  stage1d_tile<MATH, FLUX, STAGE, T>(a, (long long)blockIdx.x * T, blockIdx.x == 0, sm, phase);
+}
+
+// Batched stage: a persistent grid walks a table of (problem, tile) work items over many
+// independent problems, each with its own grid, boundary conditions, alphas and dt.
+template <class MATH, int FLUX, int STAGE, int T>
+__global__ void __launch_bounds__(Tile1D<T, FluxM<FLUX>::m>::NT) stage1d_batched_kernel(const BatchArgs b) {
+  using TL = Tile1D<T, FluxM<FLUX>::m>;
+  extern __shared__ __align__(16) double sm[];
+  if (threadIdx.x == 0) mbar_init(reinterpret_cast<uint64_t*>(sm + TL::kBar), 1);
+  __syncthreads();
+  uint32_t phase = 0;
+  for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
+    const int2 item = b.tiles[t];
+    const BatchSeg sg = b.segs[item.x];
+    Stage1DArgs a;
+    a.uin = b.uin + sg.poff;
+    a.un = b.un + sg.poff;
+    a.uout = b.uout + sg.poff;
+    a.Lout = nullptr;
+    a.n = sg.n;
+    a.pitch = b.pitch;
+    a.lout_stride = 0;
+    a.dx = sg.dx;
+    a.inv_dx = sg.inv_dx;
+    a.gamma = b.gamma;
+    a.adv_speed = b.adv_speed;
+    a.eps = b.eps;
+    a.alpha_R = b.alpha_R;
+    a.bc_lo = sg.bc_lo;
+    a.bc_hi = sg.bc_hi;
+    a.ctl = b.ctl + item.x;
+    const long long j0 = (long long)item.y * T;
+    if (!stage1d_tile<MATH, FLUX, STAGE, T>(a, j0, j0 == 0, sm, phase)) return;
+    __syncthreads();
   }
 }
 
@@ -355,6 +430,83 @@ cudaError_t launch_alpha1d_policy(int flux, const double* u, long long n, long l
     alpha1d_kernel<MATH, WT_FLUX_ADVECTION><<<(unsigned)blocks, 256, 0, st>>>(u, n, pitch, gamma, adv, ctl, slot);
   else if (flux == WT_FLUX_BURGERS)
     alpha1d_kernel<MATH, WT_FLUX_BURGERS><<<(unsigned)blocks, 256, 0, st>>>(u, n, pitch, gamma, adv, ctl, slot);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+template <class MATH, int FLUX, int STAGE, int T>
+cudaError_t launch_stage1d_batched_t(const BatchArgs& b, int grid, cudaStream_t st) {
+  using TL = Tile1D<T, FluxM<FLUX>::m>;
+  stage1d_batched_kernel<MATH, FLUX, STAGE, T><<<grid, TL::NT, TL::bytes, st>>>(b);
+  return cudaGetLastError();
+}
+
+template <class MATH, int FLUX, int T>
+cudaError_t launch_stage1d_batched_flux(int stage, const BatchArgs& b, int grid, cudaStream_t st) {
+  switch (stage) {
+    case STAGE_RK1: return launch_stage1d_batched_t<MATH, FLUX, STAGE_RK1, T>(b, grid, st);
+    case STAGE_RK2: return launch_stage1d_batched_t<MATH, FLUX, STAGE_RK2, T>(b, grid, st);
+    case STAGE_RK3: return launch_stage1d_batched_t<MATH, FLUX, STAGE_RK3, T>(b, grid, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <class MATH>
+cudaError_t launch_stage1d_batched_policy(int flux, int stage, int tile, const BatchArgs& b, int grid,
+                                          cudaStream_t st) {
+  if (flux == WT_FLUX_EULER1D) {
+    if (tile == 31) return launch_stage1d_batched_flux<MATH, WT_FLUX_EULER1D, 31>(stage, b, grid, st);
+    if (tile == 63) return launch_stage1d_batched_flux<MATH, WT_FLUX_EULER1D, 63>(stage, b, grid, st);
+    if (tile == 127) return launch_stage1d_batched_flux<MATH, WT_FLUX_EULER1D, 127>(stage, b, grid, st);
+  } else if (flux == WT_FLUX_ADVECTION) {
+    if (tile == 63) return launch_stage1d_batched_flux<MATH, WT_FLUX_ADVECTION, 63>(stage, b, grid, st);
+    if (tile == 127) return launch_stage1d_batched_flux<MATH, WT_FLUX_ADVECTION, 127>(stage, b, grid, st);
+  } else if (flux == WT_FLUX_BURGERS) {
+    if (tile == 63) return launch_stage1d_batched_flux<MATH, WT_FLUX_BURGERS, 63>(stage, b, grid, st);
+    if (tile == 127) return launch_stage1d_batched_flux<MATH, WT_FLUX_BURGERS, 127>(stage, b, grid, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <class MATH, int FLUX, int T>
+int batched_occupancy_t() {
+  using TL = Tile1D<T, FluxM<FLUX>::m>;
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, stage1d_batched_kernel<MATH, FLUX, STAGE_RK2, T>, TL::NT,
+                                                    TL::bytes) != cudaSuccess)
+    return 0;
+  return nb;
+}
+
+template <class MATH>
+int batched_occupancy_policy(int flux, int tile) {
+  if (flux == WT_FLUX_EULER1D) {
+    if (tile == 31) return batched_occupancy_t<MATH, WT_FLUX_EULER1D, 31>();
+    if (tile == 63) return batched_occupancy_t<MATH, WT_FLUX_EULER1D, 63>();
+    if (tile == 127) return batched_occupancy_t<MATH, WT_FLUX_EULER1D, 127>();
+  } else if (flux == WT_FLUX_ADVECTION) {
+    if (tile == 63) return batched_occupancy_t<MATH, WT_FLUX_ADVECTION, 63>();
+    if (tile == 127) return batched_occupancy_t<MATH, WT_FLUX_ADVECTION, 127>();
+  } else if (flux == WT_FLUX_BURGERS) {
+    if (tile == 63) return batched_occupancy_t<MATH, WT_FLUX_BURGERS, 63>();
+    if (tile == 127) return batched_occupancy_t<MATH, WT_FLUX_BURGERS, 127>();
+  }
+  return 0;
+}
+
+template <class MATH>
+cudaError_t launch_alpha1d_batched_policy(int flux, const double* u, long long pitch, const BatchSeg* segs, int nprob,
+                                          long long maxn, double gamma, double adv, Ctl* ctl, cudaStream_t st) {
+  long long bx = (maxn + 255) / 256;
+  if (bx > 64) bx = 64;
+  dim3 grid((unsigned)(bx < 1 ? 1 : bx), (unsigned)nprob);
+  if (flux == WT_FLUX_EULER1D)
+    alpha1d_batched_kernel<MATH, WT_FLUX_EULER1D><<<grid, 256, 0, st>>>(u, pitch, segs, gamma, adv, ctl);
+  else if (flux == WT_FLUX_ADVECTION)
+    alpha1d_batched_kernel<MATH, WT_FLUX_ADVECTION><<<grid, 256, 0, st>>>(u, pitch, segs, gamma, adv, ctl);
+  else if (flux == WT_FLUX_BURGERS)
+    alpha1d_batched_kernel<MATH, WT_FLUX_BURGERS><<<grid, 256, 0, st>>>(u, pitch, segs, gamma, adv, ctl);
   else
     return cudaErrorInvalidValue;
   return cudaGetLastError();

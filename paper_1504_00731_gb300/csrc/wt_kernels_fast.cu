@@ -52,6 +52,64 @@ cudaError_t launch_unpack1d(const double* src, long long pitch, double* dst, lon
   return cudaGetLastError();
 }
 
+__global__ void pack1d_batched_kernel(const double* __restrict__ src, long long src_stride, double* __restrict__ dst,
+                                      long long pitch, const BatchSeg* __restrict__ segs, int m, int flip_comp) {
+  const BatchSeg sg = segs[blockIdx.y];
+  const long long row = sg.n + 2 * G;
+  const long long total = (long long)m * row;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(idx / row);
+    const long long p = idx - (long long)c * row;
+    const long long j = p - G;
+    bool flip = false;
+    const long long sj = (j >= 0 && j < sg.n) ? j : ghost_source(j, sg.n, sg.bc_lo, sg.bc_hi, &flip);
+    double v = src[c * src_stride + sg.uoff + sj];
+    if (flip && c == flip_comp) v = -v;
+    dst[c * pitch + sg.poff + p] = v;
+  }
+}
+
+__global__ void unpack1d_batched_kernel(const double* __restrict__ src, long long pitch, double* __restrict__ dst,
+                                        long long dst_stride, const BatchSeg* __restrict__ segs, int m) {
+  const BatchSeg sg = segs[blockIdx.y];
+  const long long total = (long long)m * sg.n;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(idx / sg.n);
+    const long long j = idx - (long long)c * sg.n;
+    dst[c * dst_stride + sg.uoff + j] = src[c * pitch + sg.poff + j + G];
+  }
+}
+
+__global__ void gather_t_kernel(const Ctl* __restrict__ ctl, int nprob, double* __restrict__ t_out) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < nprob) t_out[p] = ctl[p].t;
+}
+
+static dim3 batched_grid(long long maxn, int m, int nprob) {
+  long long bx = ((long long)m * (maxn + 2 * G) + 255) / 256;
+  if (bx > 64) bx = 64;
+  return dim3((unsigned)(bx < 1 ? 1 : bx), (unsigned)nprob);
+}
+
+cudaError_t launch_pack1d_batched(const double* src, long long src_stride, double* dst, long long pitch,
+                                  const BatchSeg* segs, int nprob, long long maxn, int m, int flip_comp, cudaStream_t st) {
+  pack1d_batched_kernel<<<batched_grid(maxn, m, nprob), 256, 0, st>>>(src, src_stride, dst, pitch, segs, m, flip_comp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unpack1d_batched(const double* src, long long pitch, double* dst, long long dst_stride,
+                                    const BatchSeg* segs, int nprob, long long maxn, int m, cudaStream_t st) {
+  unpack1d_batched_kernel<<<batched_grid(maxn, m, nprob), 256, 0, st>>>(src, pitch, dst, dst_stride, segs, m);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_t(const Ctl* ctl, int nprob, double* t_out, cudaStream_t st) {
+  gather_t_kernel<<<(nprob + 255) / 256, 256, 0, st>>>(ctl, nprob, t_out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_stage1d_fast(int flux, int stage, int tile, const Stage1DArgs& a, cudaStream_t st) {
   return launch_stage1d_policy<FastMath>(flux, stage, tile, a, st);
 }
@@ -60,5 +118,16 @@ cudaError_t launch_alpha1d_fast(int flux, const double* u, long long n, long lon
                                 Ctl* ctl, int slot, cudaStream_t st) {
   return launch_alpha1d_policy<FastMath>(flux, u, n, pitch, gamma, adv, ctl, slot, st);
 }
+
+cudaError_t launch_stage1d_batched_fast(int flux, int stage, int tile, const BatchArgs& b, int grid, cudaStream_t st) {
+  return launch_stage1d_batched_policy<FastMath>(flux, stage, tile, b, grid, st);
+}
+
+cudaError_t launch_alpha1d_batched_fast(int flux, const double* u, long long pitch, const BatchSeg* segs, int nprob,
+                                        long long maxn, double gamma, double adv, Ctl* ctl, cudaStream_t st) {
+  return launch_alpha1d_batched_policy<FastMath>(flux, u, pitch, segs, nprob, maxn, gamma, adv, ctl, st);
+}
+
+int stage1d_batched_occupancy_fast(int flux, int tile) { return batched_occupancy_policy<FastMath>(flux, tile); }
 
 }  // namespace wt

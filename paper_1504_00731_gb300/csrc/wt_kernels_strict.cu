@@ -14,4 +14,15 @@ cudaError_t launch_alpha1d_strict(int flux, const double* u, long long n, long l
   return launch_alpha1d_policy<StrictMath>(flux, u, n, pitch, gamma, adv, ctl, slot, st);
 }
 
+cudaError_t launch_stage1d_batched_strict(int flux, int stage, int tile, const BatchArgs& b, int grid, cudaStream_t st) {
+  return launch_stage1d_batched_policy<StrictMath>(flux, stage, tile, b, grid, st);
+}
+
+cudaError_t launch_alpha1d_batched_strict(int flux, const double* u, long long pitch, const BatchSeg* segs, int nprob,
+                                        long long maxn, double gamma, double adv, Ctl* ctl, cudaStream_t st) {
+  return launch_alpha1d_batched_policy<StrictMath>(flux, u, pitch, segs, nprob, maxn, gamma, adv, ctl, st);
+}
+
+int stage1d_batched_occupancy_strict(int flux, int tile) { return batched_occupancy_policy<StrictMath>(flux, tile); }
+
 }  // namespace wt

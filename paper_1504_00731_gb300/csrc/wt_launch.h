@@ -24,6 +24,44 @@ struct Stage1DArgs {
   Ctl* ctl;
 };
 
+// One problem of a batch: padded storage at poff in the workspace planes, caller storage
+// at uoff in the caller's packed planes.
+struct BatchSeg {
+  long long poff;
+  long long uoff;
+  long long n;
+  double dx, inv_dx;
+  int bc_lo, bc_hi;
+};
+
+// Arguments of one batched stage launch.
+struct BatchArgs {
+  const double* uin;       // plane bases [m][pitch]; problem p starts at segs[p].poff
+  const double* un;
+  double* uout;
+  long long pitch;
+  const BatchSeg* segs;
+  Ctl* ctl;                // [nprob]
+  const int2* tiles;       // work items: (problem, tile index); tile j0 = index * T
+  int ntiles;
+  double gamma, adv_speed, eps, alpha_R;
+};
+
+cudaError_t launch_stage1d_batched_strict(int flux, int stage, int tile, const BatchArgs& b, int grid, cudaStream_t st);
+cudaError_t launch_stage1d_batched_fast(int flux, int stage, int tile, const BatchArgs& b, int grid, cudaStream_t st);
+// resident CTAs per SM of the batched stage kernel (occupancy), 0 on error
+int stage1d_batched_occupancy_strict(int flux, int tile);
+int stage1d_batched_occupancy_fast(int flux, int tile);
+cudaError_t launch_alpha1d_batched_strict(int flux, const double* u, long long pitch, const BatchSeg* segs, int nprob,
+                                          long long maxn, double gamma, double adv, Ctl* ctl, cudaStream_t st);
+cudaError_t launch_alpha1d_batched_fast(int flux, const double* u, long long pitch, const BatchSeg* segs, int nprob,
+                                        long long maxn, double gamma, double adv, Ctl* ctl, cudaStream_t st);
+cudaError_t launch_pack1d_batched(const double* src, long long src_stride, double* dst, long long pitch,
+                                  const BatchSeg* segs, int nprob, long long maxn, int m, int flip_comp, cudaStream_t st);
+cudaError_t launch_unpack1d_batched(const double* src, long long pitch, double* dst, long long dst_stride,
+                                    const BatchSeg* segs, int nprob, long long maxn, int m, cudaStream_t st);
+cudaError_t launch_gather_t(const Ctl* ctl, int nprob, double* t_out, cudaStream_t st);
+
 // Records a message for wt_last_error() on the calling thread and returns code.
 int set_last_error(int code, const char* msg);
 

@@ -166,7 +166,7 @@ def test_euler_full_size_fast_run(wtlib, oracle):
     outflow, seeded Riemann + entropy-wave data, CFL 0.5, 2000 RK steps, fast mode."""
     b, O = wtlib, oracle
     U, x, dx = W.euler_c2(4096, seed=0)
-    prob = b.problem(b.WT_FLUX_EULER1D, bc=b.WT_BC_OUTFLOW)
+    prob = b.problem(b.WT_FLUX_EULER1D, bc=b.WT_BC_OUTFLOW, alpha_R=W.ALPHA_R_SEEDED)
     u, t, s = _gpu_run(b, prob, U, -5.0, 5.0, cfl=0.5, max_steps=2000)
     ref, t_ref, s_ref = O.run(_oracle_problem(O, b, prob), U, dx, cfl=0.5, n_steps=2000)
     assert s == s_ref == 2000
