@@ -96,6 +96,7 @@ def lib():
     L.wto_roe_eigen.argtypes = [ctypes.c_int32, P, P, D, ctypes.c_int32, P, P]
     L.wto_alpha.argtypes = [PP, I64, I64, D, D, P, D, P, P]
     L.wto_rhs.argtypes = [PP, I64, I64, D, D, P, P, PI64, PI64]
+    L.wto_rhs_at.argtypes = [PP, I64, I64, D, D, P, P, PI64, I64, P]
     L.wto_rhs_jvp.argtypes = [PP, I64, I64, D, D, P, P, P, P]
     L.wto_run.argtypes = [PP, I64, I64, D, D, P, D, D, D, I64, P, PI64]
     L.wto_run_jvp.argtypes = [PP, I64, I64, D, D, P, P, D, D, D, I64, P, PI64]
@@ -166,6 +167,19 @@ def rhs(prob, u, dx, dy=1.0, counts=False):
     lib().wto_rhs(ctypes.byref(prob), nx, ny, dx, dy, _ptr(u), _ptr(out), ctypes.byref(t1), ctypes.byref(rs))
     if counts:
         return out, t1.value, rs.value
+    return out
+
+
+def rhs_at(prob, u, cells, dx, dy=1.0, alpha8=None):
+    """L(u) at flat cell indices (y * nx + x) only; alpha8 defaults to the state's own alphas."""
+    u, nx, ny = _dims(u)
+    if alpha8 is None:
+        alpha8, _ = alpha(prob, u, dx, dy)
+    a = np.ascontiguousarray(alpha8, dtype=np.float64).reshape(8)
+    cells = np.ascontiguousarray(cells, dtype=np.int64)
+    out = np.zeros((cells.size, u.shape[0]))
+    lib().wto_rhs_at(ctypes.byref(prob), nx, ny, dx, dy, _ptr(u), _ptr(a),
+                     cells.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), cells.size, _ptr(out))
     return out
 
 

@@ -755,6 +755,38 @@ void wto_rhs(const Problem* P, int64_t nx, int64_t ny, double dx, double dy, con
   if (restricted) *restricted = rs;
 }
 
+/* L(u) at selected cells only (cells[k] = y * nx + x), with the Lax-Friedrichs constants
+ * alpha8[dir * 4 + s] of the whole state given (wto_alpha computes them).  Each sampled cell
+ * takes the interface fluxes of its own row and column, computed exactly as in rhs(). */
+void wto_rhs_at(const Problem* P, int64_t nx, int64_t ny, double dx, double dy, const double* u, const double* alpha8,
+                const int64_t* cells, int64_t ncells, double* out) {
+  const int m = P->m;
+  const int64_t all = nx * ny;
+  std::vector<double> hF;
+  for (int64_t q = 0; q < ncells; ++q) {
+    const int64_t y = cells[q] / nx, x = cells[q] - y * nx;
+    Line<double> row(m, (int)nx);
+    for (int c = 0; c < m; ++c)
+      for (int64_t i = 0; i < nx; ++i) row.at(c, (int)i) = u[(size_t)c * all + y * nx + i];
+    fill_ghosts(row, P->bc_lo[0], P->bc_hi[0], 1);
+    line_fluxes(*P, row, 0, alpha8, hF, (long long*)0, (long long*)0);
+    for (int c = 0; c < m; ++c) {
+      double hp = hF[(size_t)c * (nx + 1) + (x + 1)], hm = hF[(size_t)c * (nx + 1) + x];
+      out[q * m + c] = -(hp - hm) / dx;
+    }
+    if (ndim_of(*P) == 1) continue;
+    Line<double> col(m, (int)ny);
+    for (int c = 0; c < m; ++c)
+      for (int64_t j = 0; j < ny; ++j) col.at(c, (int)j) = u[(size_t)c * all + j * nx + x];
+    fill_ghosts(col, P->bc_lo[1], P->bc_hi[1], 2);
+    line_fluxes(*P, col, 1, alpha8 + 4, hF, (long long*)0, (long long*)0);
+    for (int c = 0; c < m; ++c) {
+      double hp = hF[(size_t)c * (ny + 1) + (y + 1)], hm = hF[(size_t)c * (ny + 1) + y];
+      out[q * m + c] = out[q * m + c] + (-(hp - hm) / dy);
+    }
+  }
+}
+
 /* Forward-mode derivative of L at u in direction du. */
 void wto_rhs_jvp(const Problem* P, int64_t nx, int64_t ny, double dx, double dy, const double* u, const double* du,
                  double* L, double* dL) {

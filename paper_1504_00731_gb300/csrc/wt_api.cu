@@ -69,10 +69,22 @@ int check_problem(const wt_problem* p) {
   return WT_OK;
 }
 
+int check_grid_2d(const wt_problem* p, const wt_grid* g) {
+  if (g->ndim != 2) return fail(WT_ERR_ARG, "ndim must be 2 for 2D Euler");
+  for (int d = 0; d < 2; ++d) {
+    if (g->n[d] < G) return fail(WT_ERR_ARG, "n[%d] = %lld is below the minimum of %d cells", d, (long long)g->n[d], G);
+    if (g->n[d] > (1LL << 20)) return fail(WT_ERR_ARG, "n[%d] too large", d);
+    if (!(g->hi[d] > g->lo[d]) || !std::isfinite(g->hi[d] - g->lo[d])) return fail(WT_ERR_ARG, "need lo < hi");
+    if ((p->bc_lo[d] == WT_BC_PERIODIC) != (p->bc_hi[d] == WT_BC_PERIODIC))
+      return fail(WT_ERR_ARG, "a periodic boundary must be periodic at both ends");
+  }
+  return WT_OK;
+}
+
 int check_grid_1d(const wt_problem* p, const wt_grid* g) {
   if (!g) return fail(WT_ERR_ARG, "grid is NULL");
   if (g->reserved != 0) return fail(WT_ERR_ARG, "reserved field must be 0");
-  if (p->flux == WT_FLUX_EULER2D) return fail(WT_ERR_UNSUPPORTED, "2D Euler is not available in this build");
+  if (p->flux == WT_FLUX_EULER2D) return check_grid_2d(p, g);
   if (g->ndim != 1) return fail(WT_ERR_ARG, "ndim must be 1 for a 1D flux");
   if (g->n[0] < G) return fail(WT_ERR_ARG, "n = %lld is below the minimum of %d cells", (long long)g->n[0], G);
   if (g->n[0] > (1LL << 40)) return fail(WT_ERR_ARG, "n too large");
@@ -402,6 +414,227 @@ int get_batched_graph(const wt_problem* p, int device, int tile, int grid, const
   return WT_OK;
 }
 
+
+// --- 2D ------------------------------------------------------------------------------------
+
+// 2D workspace: [Ctl][Un][U1][U2][staging 4*nx*ny][staging 4*nx*ny]; padded planes with row
+// stride rowp = nx + 6 rounded up to even and plane stride (ny + 6) * rowp rounded to 32.
+struct Layout2D {
+  size_t ctl, un, u1, u2, st_in, st_out, total;
+  long long rowp, planep;
+};
+
+Layout2D layout_2d(long long nx, long long ny) {
+  Layout2D L;
+  L.rowp = ((nx + 2 * G + 1) / 2) * 2;
+  L.planep = (((ny + 2 * G) * L.rowp + 31) / 32) * 32;
+  const size_t planes = (size_t)4 * L.planep * sizeof(double);
+  const size_t stage = (size_t)4 * nx * ny * sizeof(double);
+  size_t o = 0;
+  L.ctl = o;
+  o = align_up(o + sizeof(Ctl));
+  L.un = o;
+  o = align_up(o + planes);
+  L.u1 = o;
+  o = align_up(o + planes);
+  L.u2 = o;
+  o = align_up(o + planes);
+  L.st_in = o;
+  o = align_up(o + stage);
+  L.st_out = o;
+  o = align_up(o + stage);
+  L.total = o;
+  return L;
+}
+
+Stage2DArgs base_args_2d(const wt_problem* p, const wt_grid* g, const Layout2D& lay, Ctl* ctl) {
+  Stage2DArgs a;
+  memset(&a, 0, sizeof a);
+  a.nx = g->n[0];
+  a.ny = g->n[1];
+  a.rowp = lay.rowp;
+  a.planep = lay.planep;
+  a.dx = (g->hi[0] - g->lo[0]) / (double)g->n[0];
+  a.dy = (g->hi[1] - g->lo[1]) / (double)g->n[1];
+  a.inv_dx = 1.0 / a.dx;
+  a.inv_dy = 1.0 / a.dy;
+  a.gamma = p->gamma;
+  a.eps = p->eps;
+  a.alpha_R = p->alpha_R;
+  a.bcx_lo = p->bc_lo[0];
+  a.bcx_hi = p->bc_hi[0];
+  a.bcy_lo = p->bc_lo[1];
+  a.bcy_hi = p->bc_hi[1];
+  a.ctl = ctl;
+  return a;
+}
+
+cudaError_t launch_stage2d(const wt_problem* p, int stage, const Stage2DArgs& a, cudaStream_t st) {
+  return p->mode == WT_MODE_STRICT ? launch_stage2d_strict(stage, a, st) : launch_stage2d_fast(stage, a, st);
+}
+
+cudaError_t launch_alpha2d(const wt_problem* p, const Stage2DArgs& a, const double* u, cudaStream_t st) {
+  return p->mode == WT_MODE_STRICT
+             ? launch_alpha2d_strict(u, a.nx, a.ny, a.rowp, a.planep, a.gamma, a.dx, a.dy, a.ctl, 0, st)
+             : launch_alpha2d_fast(u, a.nx, a.ny, a.rowp, a.planep, a.gamma, a.dx, a.dy, a.ctl, 0, st);
+}
+
+struct Graph2D {
+  Stage2DArgs a[3];
+  int mode, device;
+  cudaGraphExec_t exec;
+};
+std::vector<Graph2D> g_graphs2d;
+
+int get_step_graph_2d(const wt_problem* p, int device, const Stage2DArgs a[3], cudaGraphExec_t* out) {
+  std::lock_guard<std::mutex> lk(g_graph_mu);
+  for (auto& e : g_graphs2d)
+    if (e.device == device && e.mode == p->mode && !memcmp(e.a, a, sizeof e.a)) {
+      *out = e.exec;
+      return WT_OK;
+    }
+  if (device < 0 || device >= 64) return fail(WT_ERR_CUDA, "device index %d out of range", device);
+  cudaStream_t& cs = g_capture_stream[device];
+  if (!cs) WT_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  WT_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  cudaError_t le = cudaSuccess;
+  for (int s = 0; s < 3 && le == cudaSuccess; ++s) le = launch_stage2d(p, s, a[s], cs);
+  cudaGraph_t graph = nullptr;
+  cudaError_t ee = cudaStreamEndCapture(cs, &graph);
+  if (le != cudaSuccess) return fail(WT_ERR_CUDA, "2D stage launch during capture: %s", cudaGetErrorString(le));
+  if (ee != cudaSuccess) return fail(WT_ERR_CUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(ee));
+  cudaGraphExec_t exec = nullptr;
+  cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ie != cudaSuccess) return fail(WT_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(ie));
+  if (g_graphs2d.size() >= 8) {
+    cudaGraphExecDestroy(g_graphs2d.front().exec);
+    g_graphs2d.erase(g_graphs2d.begin());
+  }
+  Graph2D e;
+  memcpy(e.a, a, sizeof e.a);
+  e.mode = p->mode;
+  e.device = device;
+  e.exec = exec;
+  g_graphs2d.push_back(e);
+  *out = exec;
+  return WT_OK;
+}
+
+int rhs_2d(const wt_problem* prob, const wt_grid* grid, const double* u, double* L, void* ws, size_t ws_bytes,
+           void* stream) {
+  int rc;
+  const Layout2D lay = layout_2d(grid->n[0], grid->n[1]);
+  int dev;
+  if ((rc = check_ws(ws, ws_bytes, lay.total, &dev)) != WT_OK) return rc;
+  DeviceGuard guard;
+  if ((rc = guard.enter(dev)) != WT_OK) return rc;
+  WT_CUDA(prob->mode == WT_MODE_STRICT ? prepare_stage2d_strict() : prepare_stage2d_fast());
+  bool u_dev, L_dev;
+  int d_u, d_L;
+  pointer_info(u, &u_dev, &d_u);
+  pointer_info(L, &L_dev, &d_L);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char* w = static_cast<char*>(ws);
+  Ctl* ctl = reinterpret_cast<Ctl*>(w + lay.ctl);
+  double* Un = reinterpret_cast<double*>(w + lay.un);
+  double* st_in = reinterpret_cast<double*>(w + lay.st_in);
+  double* st_out = reinterpret_cast<double*>(w + lay.st_out);
+  const long long cells = grid->n[0] * grid->n[1];
+  Stage2DArgs a = base_args_2d(prob, grid, lay, ctl);
+  WT_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl), st));
+  const double* src = u;
+  if (!u_dev) {
+    WT_CUDA(cudaMemcpyAsync(st_in, u, sizeof(double) * 4 * cells, cudaMemcpyHostToDevice, st));
+    src = st_in;
+  }
+  WT_CUDA(launch_pack2d(src, Un, a.nx, a.ny, a.rowp, a.planep, a.bcx_lo, a.bcx_hi, a.bcy_lo, a.bcy_hi, st));
+  WT_CUDA(launch_alpha2d(prob, a, Un, st));
+  a.uin = Un;
+  a.Lout = L_dev ? L : st_out;
+  WT_CUDA(launch_stage2d(prob, STAGE_RHS, a, st));
+  if (!L_dev) WT_CUDA(cudaMemcpyAsync(L, st_out, sizeof(double) * 4 * cells, cudaMemcpyDeviceToHost, st));
+  if (!u_dev || !L_dev) {
+    WT_CUDA(cudaStreamSynchronize(st));
+    int status = 0;
+    WT_CUDA(cudaMemcpy(&status, &ctl->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (status != 0) return fail(status, "device reported status %d (non-finite state)", status);
+  }
+  return WT_OK;
+}
+
+int step_2d(const wt_problem* prob, const wt_grid* grid, double* u, double cfl, double dt_fixed, double t_final,
+            int64_t max_steps, double* t_reached, int64_t* steps, void* ws, size_t ws_bytes, void* stream) {
+  int rc;
+  const Layout2D lay = layout_2d(grid->n[0], grid->n[1]);
+  int dev;
+  if ((rc = check_ws(ws, ws_bytes, lay.total, &dev)) != WT_OK) return rc;
+  DeviceGuard guard;
+  if ((rc = guard.enter(dev)) != WT_OK) return rc;
+  WT_CUDA(prob->mode == WT_MODE_STRICT ? prepare_stage2d_strict() : prepare_stage2d_fast());
+  bool u_dev;
+  int d_u;
+  pointer_info(u, &u_dev, &d_u);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char* w = static_cast<char*>(ws);
+  Ctl* ctl = reinterpret_cast<Ctl*>(w + lay.ctl);
+  double* Un = reinterpret_cast<double*>(w + lay.un);
+  double* U1 = reinterpret_cast<double*>(w + lay.u1);
+  double* U2 = reinterpret_cast<double*>(w + lay.u2);
+  double* st_in = reinterpret_cast<double*>(w + lay.st_in);
+  const long long cells = grid->n[0] * grid->n[1];
+  const Ctl h = make_ctl(cfl, dt_fixed, t_final);
+  WT_CUDA(cudaMemcpyAsync(ctl, &h, sizeof(Ctl), cudaMemcpyHostToDevice, st));
+  Stage2DArgs base = base_args_2d(prob, grid, lay, ctl);
+  const double* src = u;
+  if (!u_dev) {
+    WT_CUDA(cudaMemcpyAsync(st_in, u, sizeof(double) * 4 * cells, cudaMemcpyHostToDevice, st));
+    src = st_in;
+  }
+  WT_CUDA(launch_pack2d(src, Un, base.nx, base.ny, base.rowp, base.planep, base.bcx_lo, base.bcx_hi, base.bcy_lo,
+                        base.bcy_hi, st));
+  WT_CUDA(launch_alpha2d(prob, base, Un, st));
+  Stage2DArgs a[3] = {base, base, base};
+  a[0].uin = Un;
+  a[0].uout = U1;
+  a[1].uin = U1;
+  a[1].un = Un;
+  a[1].uout = U2;
+  a[2].uin = U2;
+  a[2].un = Un;
+  a[2].uout = Un;
+  cudaGraphExec_t exec;
+  if (max_steps > 0 && (rc = get_step_graph_2d(prob, dev, a, &exec)) != WT_OK) return rc;
+  Ctl hc;
+  int64_t launched = 0;
+  const bool bounded_time = std::isfinite(t_final);
+  const int64_t chunk = bounded_time ? 16 : max_steps;
+  while (launched < max_steps) {
+    int64_t k = max_steps - launched;
+    if (k > chunk) k = chunk;
+    for (int64_t i = 0; i < k; ++i) WT_CUDA(cudaGraphLaunch(exec, st));
+    launched += k;
+    if (bounded_time) {
+      WT_CUDA(cudaMemcpyAsync(&hc, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+      WT_CUDA(cudaStreamSynchronize(st));
+      if (hc.status != 0 || !(hc.t < hc.t_final)) break;
+    }
+  }
+  WT_CUDA(cudaMemcpyAsync(&hc, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+  WT_CUDA(cudaStreamSynchronize(st));
+  if (hc.status != 0) return fail(hc.status, "device reported status %d after %lld steps", hc.status, hc.steps);
+  if (u_dev) {
+    WT_CUDA(launch_unpack2d(Un, u, base.nx, base.ny, base.rowp, base.planep, st));
+  } else {
+    WT_CUDA(launch_unpack2d(Un, st_in, base.nx, base.ny, base.rowp, base.planep, st));
+    WT_CUDA(cudaMemcpyAsync(u, st_in, sizeof(double) * 4 * cells, cudaMemcpyDeviceToHost, st));
+  }
+  WT_CUDA(cudaStreamSynchronize(st));
+  if (t_reached) *t_reached = hc.t;
+  if (steps) *steps = hc.steps;
+  return WT_OK;
+}
+
 }  // namespace
 
 int wt::set_last_error(int code, const char* msg) { return fail(code, "%s", msg); }
@@ -414,6 +647,7 @@ size_t wt_workspace_bytes(const wt_problem* prob, const wt_grid* grid, int64_t b
   if (check_problem(prob) != WT_OK) return 0;
   if (grid) {
     if (check_grid_1d(prob, grid) != WT_OK) return 0;
+    if (grid->ndim == 2) return layout_2d(grid->n[0], grid->n[1]).total;
     return layout_1d(prob->m, grid->n[0]).total;
   }
   if (prob->flux == WT_FLUX_EULER2D) {
@@ -435,6 +669,7 @@ int weno_theta_rhs(const wt_problem* prob, const wt_grid* grid, const double* u,
   if ((rc = check_problem(prob)) != WT_OK) return rc;
   if ((rc = check_grid_1d(prob, grid)) != WT_OK) return rc;
   if (!u || !L) return fail(WT_ERR_ARG, "u and L must not be NULL");
+  if (grid->ndim == 2) return rhs_2d(prob, grid, u, L, ws, ws_bytes, stream);
   const int m = prob->m;
   const long long n = grid->n[0];
   const Layout1D lay = layout_1d(m, n);
@@ -483,6 +718,8 @@ int weno_theta_step(const wt_problem* prob, const wt_grid* grid, double* u, doub
   if (max_steps < 0) return fail(WT_ERR_ARG, "max_steps must be >= 0");
   if (!(dt_fixed > 0.0) && !(cfl > 0.0 && std::isfinite(cfl))) return fail(WT_ERR_ARG, "need cfl > 0 or dt_fixed > 0");
   if (!(t_final > 0.0) && !(t_final == 0.0)) return fail(WT_ERR_ARG, "t_final must be >= 0");
+  if (grid->ndim == 2)
+    return step_2d(prob, grid, u, cfl, dt_fixed, t_final, max_steps, t_reached, steps, ws, ws_bytes, stream);
   const int m = prob->m;
   const long long n = grid->n[0];
   const Layout1D lay = layout_1d(m, n);
@@ -620,7 +857,6 @@ int weno_theta_step_batched(const wt_problem* prob, const wt_segment* segs, int3
   double* U1 = reinterpret_cast<double*>(w + lay.u1);
   double* U2 = reinterpret_cast<double*>(w + lay.u2);
   double* st_u = reinterpret_cast<double*>(w + lay.st_u);
-  double* st_t = reinterpret_cast<double*>(w + lay.st_t);
 
   std::vector<Ctl> hctl(nprob, make_ctl(cfl, 0.0, INFINITY));
   WT_CUDA(cudaMemcpyAsync(dsegs, hs.data(), sizeof(BatchSeg) * nprob, cudaMemcpyHostToDevice, st));

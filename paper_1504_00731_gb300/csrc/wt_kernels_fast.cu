@@ -1,6 +1,7 @@
 // Fast-arithmetic instantiations of the 1D kernels, plus the boundary-fill (pack) and
 // unpack kernels, which do no arithmetic.
 #include "wt_kernels.cuh"
+#include "wt_kernels2d.cuh"
 #include "wt_math_fast.cuh"
 
 namespace wt {
@@ -129,5 +130,60 @@ cudaError_t launch_alpha1d_batched_fast(int flux, const double* u, long long pit
 }
 
 int stage1d_batched_occupancy_fast(int flux, int tile) { return batched_occupancy_policy<FastMath>(flux, tile); }
+
+__global__ void pack2d_kernel(const double* __restrict__ src, double* __restrict__ dst, long long nx, long long ny,
+                              long long rowp, long long planep, int bxl, int bxh, int byl, int byh) {
+  const long long W = nx + 2 * G, Hh = ny + 2 * G;
+  const long long per = W * Hh;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < 4 * per;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(idx / per);
+    const long long k = idx - (long long)c * per;
+    const long long py = k / W, px = k - py * W;
+    long long x = px - G, y = py - G;
+    bool fx = false, fy = false;
+    if (x < 0 || x >= nx) x = ghost_source(x, nx, bxl, bxh, &fx);
+    if (y < 0 || y >= ny) y = ghost_source(y, ny, byl, byh, &fy);
+    double v = src[(c * ny + y) * nx + x];
+    if ((fx && c == 1) || (fy && c == 2)) v = -v;  // reflective: normal momentum flips
+    dst[c * planep + py * rowp + px] = v;
+  }
+}
+
+__global__ void unpack2d_kernel(const double* __restrict__ src, double* __restrict__ dst, long long nx, long long ny,
+                                long long rowp, long long planep) {
+  const long long per = nx * ny;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < 4 * per;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(idx / per);
+    const long long k = idx - (long long)c * per;
+    const long long y = k / nx, x = k - y * nx;
+    dst[idx] = src[c * planep + (y + G) * rowp + x + G];
+  }
+}
+
+cudaError_t launch_pack2d(const double* src, double* dst, long long nx, long long ny, long long rowp, long long planep,
+                          int bxl, int bxh, int byl, int byh, cudaStream_t st) {
+  pack2d_kernel<<<copy_grid(4 * (nx + 2 * G) * (ny + 2 * G)), 256, 0, st>>>(src, dst, nx, ny, rowp, planep, bxl, bxh,
+                                                                            byl, byh);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unpack2d(const double* src, double* dst, long long nx, long long ny, long long rowp,
+                            long long planep, cudaStream_t st) {
+  unpack2d_kernel<<<copy_grid(4 * nx * ny), 256, 0, st>>>(src, dst, nx, ny, rowp, planep);
+  return cudaGetLastError();
+}
+
+cudaError_t prepare_stage2d_fast() { return prepare_stage2d_policy<FastMath>(); }
+
+cudaError_t launch_stage2d_fast(int stage, const Stage2DArgs& a, cudaStream_t st) {
+  return launch_stage2d_policy<FastMath>(stage, a, st);
+}
+
+cudaError_t launch_alpha2d_fast(const double* u, long long nx, long long ny, long long rowp, long long planep,
+                                double gamma, double dx, double dy, Ctl* ctl, int slot, cudaStream_t st) {
+  return launch_alpha2d_policy<FastMath>(u, nx, ny, rowp, planep, gamma, dx, dy, ctl, slot, st);
+}
 
 }  // namespace wt

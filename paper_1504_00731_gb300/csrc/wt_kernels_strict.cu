@@ -1,6 +1,7 @@
 // Strict-arithmetic instantiations of the 1D kernels.  Built with -fmad=false: no operation
 // is contracted, so every result equals a literal binary64 evaluation of the paper's formulas.
 #include "wt_kernels.cuh"
+#include "wt_kernels2d.cuh"
 #include "wt_math_strict.cuh"
 
 namespace wt {
@@ -24,5 +25,16 @@ cudaError_t launch_alpha1d_batched_strict(int flux, const double* u, long long p
 }
 
 int stage1d_batched_occupancy_strict(int flux, int tile) { return batched_occupancy_policy<StrictMath>(flux, tile); }
+
+cudaError_t prepare_stage2d_strict() { return prepare_stage2d_policy<StrictMath>(); }
+
+cudaError_t launch_stage2d_strict(int stage, const Stage2DArgs& a, cudaStream_t st) {
+  return launch_stage2d_policy<StrictMath>(stage, a, st);
+}
+
+cudaError_t launch_alpha2d_strict(const double* u, long long nx, long long ny, long long rowp, long long planep,
+                                double gamma, double dx, double dy, Ctl* ctl, int slot, cudaStream_t st) {
+  return launch_alpha2d_policy<StrictMath>(u, nx, ny, rowp, planep, gamma, dx, dy, ctl, slot, st);
+}
 
 }  // namespace wt

@@ -62,6 +62,34 @@ cudaError_t launch_unpack1d_batched(const double* src, long long pitch, double* 
                                     const BatchSeg* segs, int nprob, long long maxn, int m, cudaStream_t st);
 cudaError_t launch_gather_t(const Ctl* ctl, int nprob, double* t_out, cudaStream_t st);
 
+// Arguments of one fused 2D stage launch.  Padded planes: cell (x, y) at (y + G) * rowp + x + G.
+struct Stage2DArgs {
+  const double* uin;
+  const double* un;
+  double* uout;
+  double* Lout;          // RHS mode: [4][ny][nx]
+  long long nx, ny;
+  long long rowp;        // padded row stride (even)
+  long long planep;      // padded plane stride
+  double dx, dy, inv_dx, inv_dy;
+  double gamma, eps, alpha_R;
+  int bcx_lo, bcx_hi, bcy_lo, bcy_hi;
+  Ctl* ctl;
+};
+
+cudaError_t prepare_stage2d_strict();
+cudaError_t prepare_stage2d_fast();
+cudaError_t launch_stage2d_strict(int stage, const Stage2DArgs& a, cudaStream_t st);
+cudaError_t launch_stage2d_fast(int stage, const Stage2DArgs& a, cudaStream_t st);
+cudaError_t launch_alpha2d_strict(const double* u, long long nx, long long ny, long long rowp, long long planep,
+                                  double gamma, double dx, double dy, Ctl* ctl, int slot, cudaStream_t st);
+cudaError_t launch_alpha2d_fast(const double* u, long long nx, long long ny, long long rowp, long long planep,
+                                double gamma, double dx, double dy, Ctl* ctl, int slot, cudaStream_t st);
+cudaError_t launch_pack2d(const double* src, double* dst, long long nx, long long ny, long long rowp, long long planep,
+                          int bxl, int bxh, int byl, int byh, cudaStream_t st);
+cudaError_t launch_unpack2d(const double* src, double* dst, long long nx, long long ny, long long rowp,
+                            long long planep, cudaStream_t st);
+
 // Records a message for wt_last_error() on the calling thread and returns code.
 int set_last_error(int code, const char* msg);
 

@@ -162,6 +162,109 @@ struct FastMath {
   }
 
   __device__ __forceinline__ static double cfl_dt(double cfl, double dx, double smax) { return cfl * dx / smax; }
+
+  // ================================ 2D Euler (Sec. 4.3) ================================
+  __device__ __forceinline__ static void euler2d_cell(const double* U, double gamma, double* f, double* g, double& u,
+                                                      double& v, double& H, double& sr) {
+    const double ir = 1.0 / U[0];
+    u = U[1] * ir;
+    v = U[2] * ir;
+    const double p = (gamma - 1.0) * fma(-0.5 * U[1], u, fma(-0.5 * U[2], v, U[3]));
+    const double e = U[3] + p;
+    f[0] = U[1];
+    f[1] = fma(U[1], u, p);
+    f[2] = U[1] * v;
+    f[3] = e * u;
+    g[0] = U[2];
+    g[1] = f[2];
+    g[2] = fma(U[2], v, p);
+    g[3] = e * v;
+    H = e * ir;
+    sr = sqrt(U[0]);
+  }
+
+  __device__ __forceinline__ static void euler2d_speeds(const double* U, double gamma, double dx, double dy,
+                                                        double* lx, double* ly, double& q) {
+    const double ir = 1.0 / U[0];
+    const double u = U[1] * ir, v = U[2] * ir;
+    const double p = (gamma - 1.0) * fma(-0.5 * U[1], u, fma(-0.5 * U[2], v, U[3]));
+    const double c = sqrt(gamma * p * ir);
+    const double au = fabs(u), av = fabs(v);
+    lx[0] = fabs(u - c);
+    lx[1] = au;
+    lx[2] = au;
+    lx[3] = fabs(u + c);
+    ly[0] = fabs(v - c);
+    ly[1] = av;
+    ly[2] = av;
+    ly[3] = fabs(v + c);
+    q = (au + c) / dx + (av + c) / dy;
+  }
+
+  // L pre-scaled by 1/2 (the factor of Eq. (flux_split_lf))
+  __device__ __forceinline__ static void roe2d(int dir, double sa, double ua, double va, double Ha, double sb,
+                                               double ub, double vb, double Hb, double gamma, double* L, double* rs) {
+    const double is = 1.0 / (sa + sb);
+    const double wa = sa * is, wb = sb * is;
+    const double u = fma(wa, ua, wb * ub);
+    const double v = fma(wa, va, wb * vb);
+    const double H = fma(wa, Ha, wb * Hb);
+    const double q2 = fma(u, u, v * v);
+    const double gm1 = gamma - 1.0;
+    const double c2 = gm1 * fma(-0.5, q2, H);
+    const double ic = rsqrt(c2);
+    const double c = c2 * ic;
+    const double hb1 = 0.5 * gm1 * ic * ic;
+    const double hb2 = 0.5 * q2 * hb1;
+    const double w = dir == 0 ? u : v;
+    const double wic = 0.5 * w * ic;
+    const double hb1u = hb1 * u, hb1v = hb1 * v;
+    if (dir == 0) {
+      L[0] = 0.5 * (hb2 + wic); L[1] = -0.5 * (hb1u + 0.5 * ic); L[2] = -0.5 * hb1v; L[3] = 0.5 * hb1;
+      L[12] = 0.5 * (hb2 - wic); L[13] = -0.5 * (hb1u - 0.5 * ic); L[14] = -0.5 * hb1v; L[15] = 0.5 * hb1;
+      L[8] = -0.5 * v; L[9] = 0.0; L[10] = 0.5; L[11] = 0.0;
+    } else {
+      L[0] = 0.5 * (hb2 + wic); L[1] = -0.5 * hb1u; L[2] = -0.5 * (hb1v + 0.5 * ic); L[3] = 0.5 * hb1;
+      L[12] = 0.5 * (hb2 - wic); L[13] = -0.5 * hb1u; L[14] = -0.5 * (hb1v - 0.5 * ic); L[15] = 0.5 * hb1;
+      L[8] = -0.5 * u; L[9] = 0.5; L[10] = 0.0; L[11] = 0.0;
+    }
+    L[4] = 0.5 - hb2;
+    L[5] = hb1u;
+    L[6] = hb1v;
+    L[7] = -hb1;
+    rs[0] = u;
+    rs[1] = v;
+    rs[2] = H;
+    rs[3] = c;
+  }
+
+  __device__ __forceinline__ static void project4(const double* l, const double* f, const double* U, double alpha,
+                                                  double& vp, double& vm) {
+    const double a = fma(l[3], f[3], fma(l[2], f[2], fma(l[1], f[1], l[0] * f[0])));
+    const double b = fma(l[3], U[3], fma(l[2], U[2], fma(l[1], U[1], l[0] * U[0])));
+    vp = fma(alpha, b, a);
+    vm = fma(-alpha, b, a);
+  }
+
+  __device__ __forceinline__ static void backproject2d(int dir, const double* rs, const double* F, double* h) {
+    const double u = rs[0], v = rs[1], H = rs[2], c = rs[3];
+    const double s03 = F[0] + F[3], d30 = F[3] - F[0];
+    const double a = s03 + F[1];
+    h[0] = a;
+    const double hq2 = 0.5 * fma(u, u, v * v);
+    if (dir == 0) {
+      h[1] = fma(u, a, c * d30);
+      h[2] = fma(v, a, F[2]);
+      h[3] = fma(H, s03, fma(u * c, d30, fma(hq2, F[1], v * F[2])));
+    } else {
+      h[1] = fma(u, a, F[2]);
+      h[2] = fma(v, a, c * d30);
+      h[3] = fma(H, s03, fma(v * c, d30, fma(hq2, F[1], u * F[2])));
+    }
+  }
+
+  __device__ __forceinline__ static double add_sweeps(double Lx, double Ly) { return Lx + Ly; }
+  __device__ __forceinline__ static double cfl_dt_2d(double cfl, double smax) { return cfl / smax; }
 };
 
 }  // namespace wt

@@ -165,6 +165,114 @@ struct StrictMath {
   }
 
   __device__ __forceinline__ static double cfl_dt(double cfl, double dx, double smax) { return cfl * dx / smax; }
+
+  // ================================ 2D Euler (Sec. 4.3) ================================
+  // cell: u, v, p, H, sqrt(rho) and both physical fluxes f (x) and g (y)
+  __device__ __forceinline__ static void euler2d_cell(const double* U, double gamma, double* f, double* g, double& u,
+                                                      double& v, double& H, double& sr) {
+    u = U[1] / U[0];
+    v = U[2] / U[0];
+    const double p = (gamma - 1.0) * (U[3] - 0.5 * U[0] * (u * u + v * v));
+    f[0] = U[1];
+    f[1] = p + U[1] * u;
+    f[2] = U[1] * v;
+    f[3] = (U[3] + p) * u;
+    g[0] = U[2];
+    g[1] = U[2] * u;
+    g[2] = p + U[2] * v;
+    g[3] = (U[3] + p) * v;
+    H = (U[3] + p) / U[0];
+    sr = sqrt(U[0]);
+  }
+
+  // |lambda| in x (u-c, u, u, u+c) and y (v-c, v, v, v+c) and the CFL quantity
+  // (|u| + c)/dx + (|v| + c)/dy
+  __device__ __forceinline__ static void euler2d_speeds(const double* U, double gamma, double dx, double dy,
+                                                        double* lx, double* ly, double& q) {
+    const double u = U[1] / U[0];
+    const double v = U[2] / U[0];
+    const double p = (gamma - 1.0) * (U[3] - 0.5 * U[0] * (u * u + v * v));
+    const double c = sqrt(gamma * p / U[0]);
+    lx[0] = fabs(u - c);
+    lx[1] = fabs(u);
+    lx[2] = fabs(u);
+    lx[3] = fabs(u + c);
+    ly[0] = fabs(v - c);
+    ly[1] = fabs(v);
+    ly[2] = fabs(v);
+    ly[3] = fabs(v + c);
+    q = (fabs(u) + c) / dx + (fabs(v) + c) / dy;
+  }
+
+  // Roe state (u, v, H, c) and left eigenvectors L (row-major 4x4) of the Roe matrix of f
+  // (dir 0) or g (dir 1); fields ordered (w - c, w, shear, w + c), w the normal velocity.
+  __device__ __forceinline__ static void roe2d(int dir, double sa, double ua, double va, double Ha, double sb,
+                                               double ub, double vb, double Hb, double gamma, double* L, double* rs) {
+    const double u = (sa * ua + sb * ub) / (sa + sb);
+    const double v = (sa * va + sb * vb) / (sa + sb);
+    const double H = (sa * Ha + sb * Hb) / (sa + sb);
+    const double q2 = u * u + v * v;
+    const double c = sqrt((gamma - 1.0) * (H - 0.5 * q2));
+    const double b1 = (gamma - 1.0) / (c * c);
+    const double b2 = 0.5 * q2 * b1;
+    if (dir == 0) {
+      L[0] = 0.5 * (b2 + u / c); L[1] = -0.5 * (b1 * u + 1.0 / c); L[2] = -0.5 * (b1 * v); L[3] = 0.5 * b1;
+      L[4] = 1.0 - b2;           L[5] = b1 * u;                    L[6] = b1 * v;           L[7] = -b1;
+      L[8] = -v;                 L[9] = 0.0;                       L[10] = 1.0;             L[11] = 0.0;
+      L[12] = 0.5 * (b2 - u / c); L[13] = -0.5 * (b1 * u - 1.0 / c); L[14] = -0.5 * (b1 * v); L[15] = 0.5 * b1;
+    } else {
+      L[0] = 0.5 * (b2 + v / c); L[1] = -0.5 * (b1 * u); L[2] = -0.5 * (b1 * v + 1.0 / c); L[3] = 0.5 * b1;
+      L[4] = 1.0 - b2;           L[5] = b1 * u;          L[6] = b1 * v;                    L[7] = -b1;
+      L[8] = -u;                 L[9] = 1.0;             L[10] = 0.0;                      L[11] = 0.0;
+      L[12] = 0.5 * (b2 - v / c); L[13] = -0.5 * (b1 * u); L[14] = -0.5 * (b1 * v - 1.0 / c); L[15] = 0.5 * b1;
+    }
+    rs[0] = u;
+    rs[1] = v;
+    rs[2] = H;
+    rs[3] = c;
+  }
+
+  __device__ __forceinline__ static void project4(const double* l, const double* f, const double* U, double alpha,
+                                                  double& vp, double& vm) {
+    double a = l[0] * f[0];
+    double b = l[0] * U[0];
+    a = a + l[1] * f[1];
+    b = b + l[1] * U[1];
+    a = a + l[2] * f[2];
+    b = b + l[2] * U[2];
+    a = a + l[3] * f[3];
+    b = b + l[3] * U[3];
+    vp = 0.5 * (a + alpha * b);
+    vm = 0.5 * (a - alpha * b);
+  }
+
+  // h = R F with R the right eigenvectors (columns) of Roe's matrix in direction dir
+  __device__ __forceinline__ static void backproject2d(int dir, const double* rs, const double* F, double* h) {
+    const double u = rs[0], v = rs[1], H = rs[2], c = rs[3];
+    const double q2 = u * u + v * v;
+    double R[16];
+    if (dir == 0) {
+      R[0] = 1.0;       R[1] = 1.0;        R[2] = 0.0;  R[3] = 1.0;
+      R[4] = u - c;     R[5] = u;          R[6] = 0.0;  R[7] = u + c;
+      R[8] = v;         R[9] = v;          R[10] = 1.0; R[11] = v;
+      R[12] = H - u * c; R[13] = 0.5 * q2; R[14] = v;   R[15] = H + u * c;
+    } else {
+      R[0] = 1.0;       R[1] = 1.0;        R[2] = 0.0;  R[3] = 1.0;
+      R[4] = u;         R[5] = u;          R[6] = 1.0;  R[7] = u;
+      R[8] = v - c;     R[9] = v;          R[10] = 0.0; R[11] = v + c;
+      R[12] = H - v * c; R[13] = 0.5 * q2; R[14] = u;   R[15] = H + v * c;
+    }
+    for (int r = 0; r < 4; ++r) {
+      double x = R[4 * r] * F[0];
+      x = x + R[4 * r + 1] * F[1];
+      x = x + R[4 * r + 2] * F[2];
+      x = x + R[4 * r + 3] * F[3];
+      h[r] = x;
+    }
+  }
+
+  __device__ __forceinline__ static double add_sweeps(double Lx, double Ly) { return Lx + Ly; }
+  __device__ __forceinline__ static double cfl_dt_2d(double cfl, double smax) { return cfl / smax; }
 };
 
 }  // namespace wt

@@ -1,0 +1,139 @@
+"""2D Euler (dimension by dimension, Sec. 4.3) on the GPU against the oracle."""
+import numpy as np
+import pytest
+
+from paper_1504_00731_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+RHS_TOL = 1e-13
+SHOCK_L1_TOL = 1e-10
+
+
+def _oprob(O, bcx, bcy, alpha_R=50.0):
+    return O.problem(O.FLUX_EULER2D, bc=bcx, bc_y=bcy, alpha_R=alpha_R)
+
+
+def _gprob(b, bcx, bcy, mode, alpha_R=50.0):
+    return b.problem(b.WT_FLUX_EULER2D, bc=bcx, bc_y=bcy, mode=mode, alpha_R=alpha_R)
+
+
+def _gpu_rhs(b, prob, U, lo=(0.0, 0.0), hi=(1.0, 1.0)):
+    _, ny, nx = U.shape
+    g = b.grid_2d(nx, ny, lo, hi)
+    ws = b.alloc_workspace(b.workspace_bytes(prob, g))
+    u = torch.from_numpy(np.ascontiguousarray(U)).cuda()
+    L = torch.full_like(u, np.nan)
+    b.weno_theta_rhs(prob, g, u, L, ws)
+    torch.cuda.synchronize()
+    return L.cpu().numpy()
+
+
+def _gpu_run(b, prob, U, lo=(0.0, 0.0), hi=(1.0, 1.0), **kw):
+    _, ny, nx = U.shape
+    g = b.grid_2d(nx, ny, lo, hi)
+    ws = b.alloc_workspace(b.workspace_bytes(prob, g))
+    u = torch.from_numpy(np.ascontiguousarray(U)).cuda()
+    t, s = b.weno_theta_step(prob, g, u, ws=ws, **kw)
+    return u.cpu().numpy(), t, s
+
+
+def _symmetric_quadrants(n):
+    """Quadrant data mirrored about both centre lines (u odd in x, v odd in y), for reflective walls."""
+    x = (np.arange(n) + 0.5) / n
+    X, Y = np.meshgrid(x, x)
+    r = np.sqrt((X - 0.5) ** 2 + (Y - 0.5) ** 2)
+    rho = np.where(r < 0.2, 1.0, 0.125)
+    p = np.where(r < 0.2, 1.0, 0.1)
+    u = 0.1 * (X - 0.5)
+    v = 0.1 * (Y - 0.5)
+    return W.cons_2d(rho, u, v, p)
+
+
+CASES = [
+    ("periodic-33x17", 33, 17, 0, 0),
+    ("periodic-64x40", 64, 40, 0, 0),
+    ("outflow-50x9", 50, 9, 1, 1),
+    ("periodic-x-reflective-y-36x30", 36, 30, 0, 2),
+    ("reflective-3x5", 3, 5, 2, 2),
+    ("outflow-x-periodic-y-65x8", 65, 8, 1, 0),
+]
+
+
+def _case_data(nx, ny, bcx, bcy, seed):
+    if bcx == 2 or bcy == 2:
+        return _symmetric_quadrants(max(nx, ny))[:, :ny, :nx].copy()
+    U, _, _ = W.euler2d_vortices(nx, ny, seed=seed)
+    return U
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_rhs_2d_strict_bitwise_and_fast_within_tolerance(wtlib, oracle, case):
+    b, O = wtlib, oracle
+    name, nx, ny, bcx, bcy = case
+    U = _case_data(nx, ny, bcx, bcy, seed=nx + ny)
+    ref = O.rhs(_oprob(O, bcx, bcy), U, 1.0 / nx, 1.0 / ny)
+    L = _gpu_rhs(b, _gprob(b, bcx, bcy, b.WT_MODE_STRICT), U)
+    assert np.array_equal(L, ref), np.abs(L - ref).max()
+    L = _gpu_rhs(b, _gprob(b, bcx, bcy, b.WT_MODE_FAST), U)
+    scale = np.abs(ref).reshape(4, -1).max(axis=1) + 1e-300
+    err = np.abs(L - ref).reshape(4, -1).max(axis=1)
+    assert np.all(err <= RHS_TOL * scale), err / scale
+
+
+def test_step_2d_strict_bitwise_and_fast_within_tolerance(wtlib, oracle):
+    b, O = wtlib, oracle
+    for nx, ny, bcx, bcy, steps in ((40, 24, 0, 0, 12), (34, 34, 2, 2, 8), (47, 13, 1, 0, 10)):
+        U = _case_data(nx, ny, bcx, bcy, seed=7)
+        ref, t_ref, s_ref = O.run(_oprob(O, bcx, bcy, W.ALPHA_R_SEEDED), U, 1.0 / nx, 1.0 / ny, cfl=0.45,
+                                  n_steps=steps)
+        u, t, s = _gpu_run(b, _gprob(b, bcx, bcy, b.WT_MODE_STRICT, W.ALPHA_R_SEEDED), U, cfl=0.45, max_steps=steps)
+        assert s == s_ref == steps and t == t_ref
+        assert np.array_equal(u, ref), np.abs(u - ref).max()
+        u, t, s = _gpu_run(b, _gprob(b, bcx, bcy, b.WT_MODE_FAST, W.ALPHA_R_SEEDED), U, cfl=0.45, max_steps=steps)
+        l1 = (1.0 / nx) * (1.0 / ny) * np.abs(u - ref).reshape(4, -1).sum(axis=1)
+        assert np.all(l1 <= SHOCK_L1_TOL), l1
+
+
+@pytest.fixture(scope="module")
+def c4_state():
+    U, dx, dy = W.euler2d_vortices(4096, 4096, seed=0)
+    return U, dx, dy
+
+
+def test_full_size_rhs_sampled(wtlib, oracle, c4_state):
+    """4096 x 4096 periodic vortex/quadrant state (the 2D workload), one RHS evaluation in the
+    fast mode the benchmark uses; 200 sampled cells (tile corners and edges included) are
+    recomputed by the oracle with the alphas of the whole state."""
+    b, O = wtlib, oracle
+    U, dx, dy = c4_state
+    L = _gpu_rhs(b, _gprob(b, 0, 0, b.WT_MODE_FAST, W.ALPHA_R_SEEDED), U)
+    rng = np.random.default_rng(0)
+    n = 4096
+    pts = [(0, 0), (n - 1, n - 1), (31, 7), (32, 8), (n - 1, 0), (0, n - 1), (2047, 2048)]
+    pts += [(int(x), int(y)) for x, y in rng.integers(0, n, (193, 2))]
+    cells = np.array([y * n + x for x, y in pts], dtype=np.int64)
+    ref = O.rhs_at(_oprob(O, 0, 0, W.ALPHA_R_SEEDED), U, cells, dx, dy)
+    got = L.reshape(4, -1)[:, cells].T
+    scale = np.abs(ref).max(axis=0)
+    assert np.all(np.abs(got - ref).max(axis=0) <= RHS_TOL * scale)
+
+
+def test_full_size_step_properties(wtlib, c4_state):
+    """Properties that hold at any size: periodic conservation of every component, and
+    equivariance under a periodic shift of the grid (bit for bit, since every cell is
+    computed the same way wherever the tiles fall)."""
+    b = wtlib
+    U, dx, dy = c4_state
+    prob = _gprob(b, 0, 0, b.WT_MODE_FAST, W.ALPHA_R_SEEDED)
+    g = b.grid_2d(4096, 4096)
+    ws = b.alloc_workspace(b.workspace_bytes(prob, g))
+    u = torch.from_numpy(U).cuda()
+    s0 = u.sum(dim=(1, 2))
+    b.weno_theta_step(prob, g, u, 0.45, ws, max_steps=2)
+    s1 = u.sum(dim=(1, 2))
+    assert torch.all((s1 - s0).abs() <= 1e-12 * u.abs().sum(dim=(1, 2)))
+    shifted = torch.roll(torch.from_numpy(U).cuda(), shifts=(3, 5), dims=(1, 2)).contiguous()
+    b.weno_theta_step(prob, g, shifted, 0.45, ws, max_steps=2)
+    assert torch.equal(torch.roll(u, shifts=(3, 5), dims=(1, 2)), shifted)
