@@ -149,22 +149,26 @@ int weno_theta_step_batched(const wt_problem* prob, const wt_segment* segs, int3
                             size_t ws_bytes, void* stream);
 
 /*
- * Gradient of J(u(T)) with respect to u(0) through n_steps RK3 steps of
- * weno_theta_step (cfl step, t_final = +inf), by the discrete adjoint of the exact map
- * the forward pass computes (every branch -- theta, restriction, max, abs -- frozen where
- * the forward pass took it).  The forward pass keeps every checkpoint_every-th state
- * and recomputes the steps in between during the reverse sweep.
- *   u0      [m][cells] initial state (host or device)
- *   dJ_duT  [m][cells] gradient of J with respect to u(T)
- *   dJ_du0  [m][cells] out: gradient with respect to u(0)
- *   uT      [m][cells] out (may be NULL): u(T)
- * ws must hold wt_adjoint_workspace_bytes(...) bytes.  Synchronises `stream`.
+ * Gradient of J(u(T)) with respect to u(0) through n_steps RK3 steps (CFL step from u^n,
+ * t_final = +inf) of nprob independent 1D Euler problems on the same grid, by the discrete
+ * adjoint of the exact map the forward pass computes (reverse mode; every branch -- theta,
+ * restriction, maxima, absolute values -- frozen where the forward pass took it, and the
+ * derivative of a maximum sent to the first cell that attains it).  The forward pass keeps
+ * every checkpoint_every-th state; the reverse sweep recomputes each segment from its
+ * checkpoint, storing the RK stage states, and reverses it step by step.  The paper has no
+ * adjoint; this differentiates its scheme (Eqs. (3rd_RK), (mod_semi), (fh_nonlinear)).
+ *   u0      [nprob][3][n] initial states (host or device)
+ *   dJ_duT  [nprob][3][n] gradient of J with respect to u(T)
+ *   dJ_du0  [nprob][3][n] out: gradient with respect to u(0)
+ *   uT      [nprob][3][n] out (may be NULL): u(T)
+ * prob->flux must be WT_FLUX_EULER1D.  ws must hold wt_adjoint_workspace_bytes(...) bytes.
+ * Synchronises `stream`.
  */
-size_t wt_adjoint_workspace_bytes(const wt_problem* prob, const wt_grid* grid, int64_t n_steps,
+size_t wt_adjoint_workspace_bytes(const wt_problem* prob, const wt_grid* grid, int32_t nprob, int64_t n_steps,
                                   int32_t checkpoint_every);
-int weno_theta_adjoint(const wt_problem* prob, const wt_grid* grid, const double* u0, double cfl, int64_t n_steps,
-                       int32_t checkpoint_every, const double* dJ_duT, double* dJ_du0, double* uT, void* ws,
-                       size_t ws_bytes, void* stream);
+int weno_theta_adjoint(const wt_problem* prob, const wt_grid* grid, int32_t nprob, const double* u0, double cfl,
+                       int64_t n_steps, int32_t checkpoint_every, const double* dJ_duT, double* dJ_du0, double* uT,
+                       void* ws, size_t ws_bytes, void* stream);
 
 /*
  * L(u) exactly as weno_theta_rhs computes it, for callers that cannot allocate device

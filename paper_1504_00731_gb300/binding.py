@@ -99,10 +99,10 @@ def lib():
     L.weno_theta_step_batched.argtypes = [P(WtProblem), P(WtSegment), ctypes.c_int32, vp, ctypes.c_int64,
                                           ctypes.c_double, ctypes.c_int64, vp, vp, ctypes.c_size_t, vp]
     L.weno_theta_step_batched.restype = ctypes.c_int
-    L.wt_adjoint_workspace_bytes.argtypes = [P(WtProblem), P(WtGrid), ctypes.c_int64, ctypes.c_int32]
+    L.wt_adjoint_workspace_bytes.argtypes = [P(WtProblem), P(WtGrid), ctypes.c_int32, ctypes.c_int64, ctypes.c_int32]
     L.wt_adjoint_workspace_bytes.restype = ctypes.c_size_t
-    L.weno_theta_adjoint.argtypes = [P(WtProblem), P(WtGrid), vp, ctypes.c_double, ctypes.c_int64, ctypes.c_int32,
-                                     vp, vp, vp, vp, ctypes.c_size_t, vp]
+    L.weno_theta_adjoint.argtypes = [P(WtProblem), P(WtGrid), ctypes.c_int32, vp, ctypes.c_double, ctypes.c_int64,
+                                     ctypes.c_int32, vp, vp, vp, vp, ctypes.c_size_t, vp]
     L.weno_theta_adjoint.restype = ctypes.c_int
     L.weno_theta_rhs_noalloc.argtypes = [P(WtProblem), P(WtGrid), vp, vp, vp]
     L.weno_theta_rhs_noalloc.restype = ctypes.c_int
@@ -198,8 +198,8 @@ def workspace_bytes(prob: WtProblem, grid: WtGrid | None, batch_cells=0, nprob=0
     return n
 
 
-def adjoint_workspace_bytes(prob, grid, n_steps, checkpoint_every) -> int:
-    n = lib().wt_adjoint_workspace_bytes(ctypes.byref(prob), ctypes.byref(grid), n_steps, checkpoint_every)
+def adjoint_workspace_bytes(prob, grid, nprob, n_steps, checkpoint_every) -> int:
+    n = lib().wt_adjoint_workspace_bytes(ctypes.byref(prob), ctypes.byref(grid), nprob, n_steps, checkpoint_every)
     if n == 0:
         raise WenoThetaError(WT_ERR_ARG, last_error())
     return n
@@ -240,8 +240,10 @@ def weno_theta_step_batched(prob, segs, u_packed, total, cfl, n_steps, ws, t_per
                                          _nbytes(ws), _stream(stream, u_packed, ws)))
 
 
-def weno_theta_adjoint(prob, grid, u0, cfl, n_steps, checkpoint_every, dJ_duT, dJ_du0, ws, uT=None, stream=None):
-    _check(lib().weno_theta_adjoint(ctypes.byref(prob), ctypes.byref(grid), _ptr(u0)[0], cfl, n_steps,
+def weno_theta_adjoint(prob, grid, nprob, u0, cfl, n_steps, checkpoint_every, dJ_duT, dJ_du0, ws, uT=None,
+                       stream=None):
+    """Gradient dJ/du0 through n_steps RK3 steps of nprob problems ([nprob][3][n] arrays)."""
+    _check(lib().weno_theta_adjoint(ctypes.byref(prob), ctypes.byref(grid), nprob, _ptr(u0)[0], cfl, n_steps,
                                     checkpoint_every, _ptr(dJ_duT)[0], _ptr(dJ_du0)[0], _ptr(uT)[0], _ptr(ws)[0],
                                     _nbytes(ws), _stream(stream, u0, ws)))
 

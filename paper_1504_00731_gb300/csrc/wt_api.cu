@@ -635,6 +635,66 @@ int step_2d(const wt_problem* prob, const wt_grid* grid, double* u, double cfl, 
   return WT_OK;
 }
 
+
+// --- discrete adjoint ----------------------------------------------------------------------
+
+struct AdjLayout {
+  size_t ctl, segs, tiles_f, tiles_r, tstart, tcount, goff, un, u1, u2, ckpt, segu, rec_a, rec_dt, v[4], G, partial,
+      arg, dtbar, staging, total;
+  long long pitch;
+};
+
+int adjoint_layout(const wt_problem* prob, const wt_grid* grid, int nprob, int64_t n_steps, int K, AdjLayout* out) {
+  int rc;
+  if ((rc = check_problem(prob)) != WT_OK) return rc;
+  if (prob->flux != WT_FLUX_EULER1D) return fail(WT_ERR_UNSUPPORTED, "the adjoint is implemented for 1D Euler");
+  if ((rc = check_grid_1d(prob, grid)) != WT_OK) return rc;
+  if (nprob < 1 || nprob > 65535) return fail(WT_ERR_ARG, "nprob = %d outside 1..65535", nprob);
+  if (n_steps < 0) return fail(WT_ERR_ARG, "n_steps must be >= 0");
+  if (K < 1) return fail(WT_ERR_ARG, "checkpoint_every must be >= 1");
+  const long long n = grid->n[0];
+  if (n > (1LL << 30)) return fail(WT_ERR_ARG, "n too large for the adjoint");
+  const long long padded = ((n + 2 * G + 1) / 2) * 2;
+  const long long P = ((padded * nprob + 31) / 32) * 32;
+  const long long S = (n_steps + K - 1) / K;
+  const long long Kseg = std::min<long long>(K, std::max<long long>(n_steps, 1));
+  const long long ntf = (long long)nprob * ((n + 126) / 127);
+  const long long ntr = (long long)nprob * ((n + 30) / 31);
+  AdjLayout L;
+  L.pitch = P;
+  const size_t plane = sizeof(double) * 3 * (size_t)P;
+  const size_t vec = sizeof(double) * 3 * (size_t)n * nprob;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = o;
+    o = align_up(o + bytes);
+    return at;
+  };
+  L.ctl = take(sizeof(Ctl) * nprob);
+  L.segs = take(sizeof(BatchSeg) * nprob);
+  L.tiles_f = take(sizeof(int2) * ntf);
+  L.tiles_r = take(sizeof(int2) * ntr);
+  L.tstart = take(sizeof(int) * nprob);
+  L.tcount = take(sizeof(int) * nprob);
+  L.goff = take(sizeof(long long) * nprob);
+  L.un = take(plane);
+  L.u1 = take(plane);
+  L.u2 = take(plane);
+  L.ckpt = take(plane * (size_t)std::max<long long>(S, 1));
+  L.segu = take(plane * 3 * (size_t)Kseg);
+  L.rec_a = take(sizeof(double) * 12 * nprob * (size_t)Kseg);
+  L.rec_dt = take(sizeof(double) * nprob * (size_t)Kseg);
+  for (int i = 0; i < 4; ++i) L.v[i] = take(vec);
+  L.G = take(sizeof(double) * 36 * (size_t)(n + 1) * nprob);
+  L.partial = take(sizeof(double) * 4 * (size_t)ntr);
+  L.arg = take(sizeof(int) * 4 * nprob);
+  L.dtbar = take(sizeof(double) * nprob);
+  L.staging = take(vec);
+  L.total = o;
+  *out = L;
+  return WT_OK;
+}
+
 }  // namespace
 
 int wt::set_last_error(int code, const char* msg) { return fail(code, "%s", msg); }
@@ -977,19 +1037,251 @@ int weno_theta_step_batched(const wt_problem* prob, const wt_segment* segs, int3
   return WT_OK;
 }
 
-size_t wt_adjoint_workspace_bytes(const wt_problem* prob, const wt_grid* grid, int64_t n_steps,
+size_t wt_adjoint_workspace_bytes(const wt_problem* prob, const wt_grid* grid, int32_t nprob, int64_t n_steps,
                                   int32_t checkpoint_every) {
-  (void)prob; (void)grid; (void)n_steps; (void)checkpoint_every;
-  fail(WT_ERR_UNSUPPORTED, "the adjoint is not available in this build");
-  return 0;
+  AdjLayout L;
+  if (adjoint_layout(prob, grid, nprob, n_steps, checkpoint_every, &L) != WT_OK) return 0;
+  return L.total;
 }
 
-int weno_theta_adjoint(const wt_problem* prob, const wt_grid* grid, const double* u0, double cfl, int64_t n_steps,
-                       int32_t checkpoint_every, const double* dJ_duT, double* dJ_du0, double* uT, void* ws,
-                       size_t ws_bytes, void* stream) {
-  (void)prob; (void)grid; (void)u0; (void)cfl; (void)n_steps; (void)checkpoint_every; (void)dJ_duT; (void)dJ_du0;
-  (void)uT; (void)ws; (void)ws_bytes; (void)stream;
-  return fail(WT_ERR_UNSUPPORTED, "the adjoint is not available in this build");
+int weno_theta_adjoint(const wt_problem* prob, const wt_grid* grid, int32_t nprob, const double* u0, double cfl,
+                       int64_t n_steps, int32_t checkpoint_every, const double* dJ_duT, double* dJ_du0, double* uT,
+                       void* ws, size_t ws_bytes, void* stream) {
+  int rc;
+  AdjLayout lay;
+  if ((rc = adjoint_layout(prob, grid, nprob, n_steps, checkpoint_every, &lay)) != WT_OK) return rc;
+  if (!u0 || !dJ_duT || !dJ_du0) return fail(WT_ERR_ARG, "u0, dJ_duT and dJ_du0 must not be NULL");
+  if (!(cfl > 0.0) || !std::isfinite(cfl)) return fail(WT_ERR_ARG, "need cfl > 0");
+  int dev;
+  if ((rc = check_ws(ws, ws_bytes, lay.total, &dev)) != WT_OK) return rc;
+  DeviceGuard guard;
+  if ((rc = guard.enter(dev)) != WT_OK) return rc;
+  const bool strict = prob->mode == WT_MODE_STRICT;
+  WT_CUDA(strict ? prepare_adj_strict() : prepare_adj_fast());
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const long long n = grid->n[0];
+  const long long P = lay.pitch;
+  const size_t plane_bytes = sizeof(double) * 3 * (size_t)P;
+  const size_t vec_bytes = sizeof(double) * 3 * (size_t)n * nprob;
+  char* w = static_cast<char*>(ws);
+  Ctl* ctl = reinterpret_cast<Ctl*>(w + lay.ctl);
+  BatchSeg* dsegs = reinterpret_cast<BatchSeg*>(w + lay.segs);
+  int2* tiles_f = reinterpret_cast<int2*>(w + lay.tiles_f);
+  int2* tiles_r = reinterpret_cast<int2*>(w + lay.tiles_r);
+  int* tstart = reinterpret_cast<int*>(w + lay.tstart);
+  int* tcount = reinterpret_cast<int*>(w + lay.tcount);
+  long long* goff = reinterpret_cast<long long*>(w + lay.goff);
+  double* Un = reinterpret_cast<double*>(w + lay.un);
+  double* U1 = reinterpret_cast<double*>(w + lay.u1);
+  double* U2 = reinterpret_cast<double*>(w + lay.u2);
+  double* ckpt = reinterpret_cast<double*>(w + lay.ckpt);
+  double* segU = reinterpret_cast<double*>(w + lay.segu);
+  double* rec_a = reinterpret_cast<double*>(w + lay.rec_a);
+  double* rec_dt = reinterpret_cast<double*>(w + lay.rec_dt);
+  double* vX = reinterpret_cast<double*>(w + lay.v[0]);
+  double* vY = reinterpret_cast<double*>(w + lay.v[1]);
+  double* vW = reinterpret_cast<double*>(w + lay.v[2]);
+  double* vZ = reinterpret_cast<double*>(w + lay.v[3]);
+  double* Gbuf = reinterpret_cast<double*>(w + lay.G);
+  double* partial = reinterpret_cast<double*>(w + lay.partial);
+  int* arg = reinterpret_cast<int*>(w + lay.arg);
+  double* dtbar = reinterpret_cast<double*>(w + lay.dtbar);
+  double* stage_buf = reinterpret_cast<double*>(w + lay.staging);
+  auto segu = [&](int64_t k, int s) { return segU + ((size_t)k * 3 + s) * 3 * (size_t)P; };
+
+  // ---- problems, tiles (forward T = 127, reverse T = adj_tile_width(), problem-major)
+  const int Tr = adj_tile_width();
+  std::vector<BatchSeg> hs(nprob);
+  std::vector<long long> hgoff(nprob);
+  std::vector<int> hts(nprob), htc(nprob);
+  std::vector<int2> tf, tr;
+  const long long padded = ((n + 2 * G + 1) / 2) * 2;
+  for (int p = 0; p < nprob; ++p) {
+    hs[p].poff = p * padded;
+    hs[p].uoff = (long long)p * 3 * n;
+    hs[p].n = n;
+    hs[p].dx = (grid->hi[0] - grid->lo[0]) / (double)n;
+    hs[p].inv_dx = 1.0 / hs[p].dx;
+    hs[p].bc_lo = prob->bc_lo[0];
+    hs[p].bc_hi = prob->bc_hi[0];
+    hgoff[p] = (long long)p * (n + 1);
+    for (long long k = 0; k < (n + 126) / 127; ++k) tf.push_back(make_int2(p, (int)k));
+    hts[p] = (int)tr.size();
+    for (long long k = 0; k < (n + Tr - 1) / Tr; ++k) tr.push_back(make_int2(p, (int)k));
+    htc[p] = (int)tr.size() - hts[p];
+  }
+  WT_CUDA(cudaMemcpyAsync(dsegs, hs.data(), sizeof(BatchSeg) * nprob, cudaMemcpyHostToDevice, st));
+  WT_CUDA(cudaMemcpyAsync(goff, hgoff.data(), sizeof(long long) * nprob, cudaMemcpyHostToDevice, st));
+  WT_CUDA(cudaMemcpyAsync(tstart, hts.data(), sizeof(int) * nprob, cudaMemcpyHostToDevice, st));
+  WT_CUDA(cudaMemcpyAsync(tcount, htc.data(), sizeof(int) * nprob, cudaMemcpyHostToDevice, st));
+  WT_CUDA(cudaMemcpyAsync(tiles_f, tf.data(), sizeof(int2) * tf.size(), cudaMemcpyHostToDevice, st));
+  WT_CUDA(cudaMemcpyAsync(tiles_r, tr.data(), sizeof(int2) * tr.size(), cudaMemcpyHostToDevice, st));
+  std::vector<Ctl> hctl(nprob, make_ctl(cfl, 0.0, INFINITY));
+
+  // host <-> device for the caller's arrays
+  bool u0_dev, g_dev, o_dev, t_dev = true;
+  int dd;
+  pointer_info(u0, &u0_dev, &dd);
+  pointer_info(dJ_duT, &g_dev, &dd);
+  pointer_info(dJ_du0, &o_dev, &dd);
+  if (uT) pointer_info(uT, &t_dev, &dd);
+  const double* src = u0;
+  if (!u0_dev) {
+    WT_CUDA(cudaMemcpyAsync(stage_buf, u0, vec_bytes, cudaMemcpyHostToDevice, st));
+    src = stage_buf;
+  }
+  WT_CUDA(launch_pack1d_batched(src, n, Un, P, dsegs, nprob, n, 3, 1, st));
+  auto init_ctl = [&](const double* state) -> int {
+    WT_CUDA(cudaMemcpyAsync(ctl, hctl.data(), sizeof(Ctl) * nprob, cudaMemcpyHostToDevice, st));
+    WT_CUDA(strict ? launch_alpha1d_batched_strict(WT_FLUX_EULER1D, state, P, dsegs, nprob, n, prob->gamma, 0.0, ctl, st)
+                   : launch_alpha1d_batched_fast(WT_FLUX_EULER1D, state, P, dsegs, nprob, n, prob->gamma, 0.0, ctl, st));
+    return WT_OK;
+  };
+  if ((rc = init_ctl(Un)) != WT_OK) return rc;
+  auto bargs = [&](const double* in, const double* unp, double* out, const int2* tl, int nt) {
+    BatchArgs b;
+    memset(&b, 0, sizeof b);
+    b.uin = in;
+    b.un = unp;
+    b.uout = out;
+    b.pitch = P;
+    b.segs = dsegs;
+    b.ctl = ctl;
+    b.tiles = tl;
+    b.ntiles = nt;
+    b.gamma = prob->gamma;
+    b.adv_speed = 0.0;
+    b.eps = prob->eps;
+    b.alpha_R = prob->alpha_R;
+    return b;
+  };
+  const int nf = (int)tf.size(), nr = (int)tr.size();
+  const int grid_f = batched_grid_size(prob, 127, nf, dev);
+
+  // ---- forward pass with checkpoints
+  const int K = checkpoint_every;
+  const int64_t S = (n_steps + K - 1) / K;
+  {
+    BatchArgs a3[3] = {bargs(Un, nullptr, U1, tiles_f, nf), bargs(U1, Un, U2, tiles_f, nf), bargs(U2, Un, Un, tiles_f, nf)};
+    cudaGraphExec_t exec = nullptr;
+    if (n_steps > 0 && (rc = get_batched_graph(prob, dev, 127, grid_f, a3, &exec)) != WT_OK) return rc;
+    for (int64_t step = 0; step < n_steps; ++step) {
+      if (step % K == 0) WT_CUDA(cudaMemcpyAsync(ckpt + (size_t)(step / K) * 3 * P, Un, plane_bytes, cudaMemcpyDeviceToDevice, st));
+      WT_CUDA(cudaGraphLaunch(exec, st));
+    }
+  }
+  {
+    std::vector<Ctl> back(nprob);
+    WT_CUDA(cudaMemcpyAsync(back.data(), ctl, sizeof(Ctl) * nprob, cudaMemcpyDeviceToHost, st));
+    WT_CUDA(cudaStreamSynchronize(st));
+    for (int p = 0; p < nprob; ++p)
+      if (back[p].status != 0) return fail(back[p].status, "problem %d: forward pass reported status %d", p, back[p].status);
+  }
+  if (uT) {
+    if (t_dev) {
+      WT_CUDA(launch_unpack1d_batched(Un, P, uT, n, dsegs, nprob, n, 3, st));
+    } else {
+      WT_CUDA(launch_unpack1d_batched(Un, P, stage_buf, n, dsegs, nprob, n, 3, st));
+      WT_CUDA(cudaMemcpyAsync(uT, stage_buf, vec_bytes, cudaMemcpyDeviceToHost, st));
+    }
+  }
+
+  // ---- reverse sweep
+  if (g_dev) {
+    WT_CUDA(cudaMemcpyAsync(vX, dJ_duT, vec_bytes, cudaMemcpyDeviceToDevice, st));
+  } else {
+    WT_CUDA(cudaMemcpyAsync(vX, dJ_duT, vec_bytes, cudaMemcpyHostToDevice, st));
+  }
+  WT_CUDA(cudaMemsetAsync(dtbar, 0, sizeof(double) * nprob, st));
+  int occ = 0, sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  occ = 2;
+  const int grid_r = std::min(nr, occ * sms);
+  for (int64_t sg = S - 1; sg >= 0; --sg) {
+    const int64_t kseg = std::min<int64_t>(K, n_steps - sg * K);
+    // recompute the segment, keeping u^n, u^(1), u^(2) of every step and their alphas and dt
+    WT_CUDA(cudaMemcpyAsync(segu(0, 0), ckpt + (size_t)sg * 3 * P, plane_bytes, cudaMemcpyDeviceToDevice, st));
+    if ((rc = init_ctl(segu(0, 0))) != WT_OK) return rc;
+    for (int64_t k = 0; k < kseg; ++k) {
+      double* ra = rec_a + (size_t)k * 3 * 4 * nprob;
+      WT_CUDA(launch_adj_record(ctl, 0, ra, nullptr, nprob, st));
+      WT_CUDA(launch_batched_stage(prob, STAGE_RK1, 127, bargs(segu(k, 0), nullptr, segu(k, 1), tiles_f, nf), grid_f, st));
+      WT_CUDA(launch_adj_record(ctl, 1, ra + 4 * nprob, rec_dt + (size_t)k * nprob, nprob, st));
+      WT_CUDA(launch_batched_stage(prob, STAGE_RK2, 127, bargs(segu(k, 1), segu(k, 0), segu(k, 2), tiles_f, nf), grid_f, st));
+      WT_CUDA(launch_adj_record(ctl, 2, ra + 8 * nprob, nullptr, nprob, st));
+      if (k + 1 < kseg)
+        WT_CUDA(launch_batched_stage(prob, STAGE_RK3, 127, bargs(segu(k, 2), segu(k, 0), segu(k + 1, 0), tiles_f, nf), grid_f, st));
+    }
+    // reverse the steps of the segment
+    for (int64_t k = kseg - 1; k >= 0; --k) {
+      const double* ra = rec_a + (size_t)k * 3 * 4 * nprob;
+      const double* rdt = rec_dt + (size_t)k * nprob;
+      const double cLs[3] = {1.0, 0.25, 2.0 / 3.0};
+      WT_CUDA(cudaMemsetAsync(vZ, 0, vec_bytes, st));
+      for (int s = 2; s >= 0; --s) {
+        const double* in = segu(k, s);
+        const double* ubo = s == 2 ? vX : (s == 1 ? vY : vW);
+        AdjArgs aa;
+        memset(&aa, 0, sizeof aa);
+        aa.uin = in;
+        aa.pitch = P;
+        aa.segs = dsegs;
+        aa.tiles = tiles_r;
+        aa.ntiles = nr;
+        aa.ustride = n;
+        aa.ubar_out = ubo;
+        aa.alpha = ra + (size_t)s * 4 * nprob;
+        aa.dt = rdt;
+        aa.cL = cLs[s];
+        aa.gamma = prob->gamma;
+        aa.eps = prob->eps;
+        aa.alpha_R = prob->alpha_R;
+        aa.goff = goff;
+        aa.G = Gbuf;
+        aa.partial = partial;
+        WT_CUDA(strict ? launch_adj_stage_strict(aa, grid_r, st) : launch_adj_stage_fast(aa, grid_r, st));
+        GatherArgs ga;
+        memset(&ga, 0, sizeof ga);
+        ga.uin = in;
+        ga.pitch = P;
+        ga.segs = dsegs;
+        ga.goff = goff;
+        ga.G = Gbuf;
+        ga.ustride = n;
+        ga.x = ubo;
+        ga.gamma = prob->gamma;
+        if (s == 2) {  // ubar(2) = 2/3 ubar(n+1) + J^T w;  ubar(n) = 1/3 ubar(n+1)
+          ga.out = vY;
+          ga.a_self = 2.0 / 3.0;
+          ga.acc = vZ;
+          ga.a_acc = 1.0 / 3.0;
+        } else if (s == 1) {  // ubar(1) = 1/4 ubar(2) + J^T w;  ubar(n) += 3/4 ubar(2)
+          ga.out = vW;
+          ga.a_self = 0.25;
+          ga.acc = vZ;
+          ga.a_acc = 0.75;
+        } else {  // ubar(n) += ubar(1) + J^T w
+          ga.out = vZ;
+          ga.a_self = 1.0;
+          ga.accumulate = 1;
+        }
+        WT_CUDA(launch_adj_gather(ga, nprob, n, st));
+        WT_CUDA(cudaMemsetAsync(arg, 0x7f, sizeof(int) * 4 * nprob, st));
+        WT_CUDA(strict ? launch_adj_argmax_strict(in, P, dsegs, nprob, n, aa.alpha, prob->gamma, arg, st)
+                       : launch_adj_argmax_fast(in, P, dsegs, nprob, n, aa.alpha, prob->gamma, arg, st));
+        WT_CUDA(launch_adj_apply(in, P, dsegs, tstart, tcount, partial, aa.alpha, rdt, arg, ga.out, n, dtbar,
+                                 s == 0 ? 1 : 0, prob->gamma, nprob, st));
+      }
+      std::swap(vX, vZ);
+    }
+  }
+  if (o_dev) {
+    WT_CUDA(cudaMemcpyAsync(dJ_du0, vX, vec_bytes, cudaMemcpyDeviceToDevice, st));
+  } else {
+    WT_CUDA(cudaMemcpyAsync(dJ_du0, vX, vec_bytes, cudaMemcpyDeviceToHost, st));
+  }
+  WT_CUDA(cudaStreamSynchronize(st));
+  return WT_OK;
 }
 
 }  // extern "C"

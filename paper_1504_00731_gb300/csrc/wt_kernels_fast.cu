@@ -1,7 +1,9 @@
 // Fast-arithmetic instantiations of the 1D kernels, plus the boundary-fill (pack) and
 // unpack kernels, which do no arithmetic.
+#define WT_ADJOINT_COMMON_KERNELS
 #include "wt_kernels.cuh"
 #include "wt_kernels2d.cuh"
+#include "wt_adjoint.cuh"
 #include "wt_math_fast.cuh"
 
 namespace wt {
@@ -184,6 +186,40 @@ cudaError_t launch_stage2d_fast(int stage, const Stage2DArgs& a, cudaStream_t st
 cudaError_t launch_alpha2d_fast(const double* u, long long nx, long long ny, long long rowp, long long planep,
                                 double gamma, double dx, double dy, Ctl* ctl, int slot, cudaStream_t st) {
   return launch_alpha2d_policy<FastMath>(u, nx, ny, rowp, planep, gamma, dx, dy, ctl, slot, st);
+}
+
+cudaError_t prepare_adj_fast() { return prepare_adj_policy<FastMath>(); }
+
+cudaError_t launch_adj_stage_fast(const AdjArgs& a, int grid, cudaStream_t st) {
+  return launch_adj_stage_policy<FastMath>(a, grid, st);
+}
+
+cudaError_t launch_adj_argmax_fast(const double* uin, long long pitch, const BatchSeg* segs, int nprob,
+                                     long long maxn, const double* alpha, double gamma, int* arg, cudaStream_t st) {
+  return launch_adj_argmax_policy<FastMath>(uin, pitch, segs, nprob, maxn, alpha, gamma, arg, st);
+}
+
+int adj_tile_width() { return 31; }
+
+cudaError_t launch_adj_gather(const GatherArgs& a, int nprob, long long maxn, cudaStream_t st) {
+  long long bx = (maxn + 255) / 256;
+  if (bx > 64) bx = 64;
+  adj_gather_kernel<<<dim3((unsigned)(bx < 1 ? 1 : bx), (unsigned)nprob), 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adj_apply(const double* uin, long long pitch, const BatchSeg* segs, const int* tstart,
+                             const int* tcount, const double* partial, const double* alpha, const double* dt,
+                             const int* arg, double* ubar, long long ustride, double* dtbar, int final_stage,
+                             double gamma, int nprob, cudaStream_t st) {
+  adj_apply_kernel<<<(nprob + 127) / 128, 128, 0, st>>>(uin, pitch, segs, tstart, tcount, partial, alpha, dt, arg, ubar,
+                                                        ustride, dtbar, final_stage, gamma, nprob);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adj_record(const Ctl* ctl, int slot, double* alpha_out, double* dt_out, int nprob, cudaStream_t st) {
+  adj_record_kernel<<<(nprob + 127) / 128, 128, 0, st>>>(ctl, slot, alpha_out, dt_out, nprob);
+  return cudaGetLastError();
 }
 
 }  // namespace wt

@@ -2,6 +2,7 @@
 // is contracted, so every result equals a literal binary64 evaluation of the paper's formulas.
 #include "wt_kernels.cuh"
 #include "wt_kernels2d.cuh"
+#include "wt_adjoint.cuh"
 #include "wt_math_strict.cuh"
 
 namespace wt {
@@ -35,6 +36,17 @@ cudaError_t launch_stage2d_strict(int stage, const Stage2DArgs& a, cudaStream_t 
 cudaError_t launch_alpha2d_strict(const double* u, long long nx, long long ny, long long rowp, long long planep,
                                 double gamma, double dx, double dy, Ctl* ctl, int slot, cudaStream_t st) {
   return launch_alpha2d_policy<StrictMath>(u, nx, ny, rowp, planep, gamma, dx, dy, ctl, slot, st);
+}
+
+cudaError_t prepare_adj_strict() { return prepare_adj_policy<StrictMath>(); }
+
+cudaError_t launch_adj_stage_strict(const AdjArgs& a, int grid, cudaStream_t st) {
+  return launch_adj_stage_policy<StrictMath>(a, grid, st);
+}
+
+cudaError_t launch_adj_argmax_strict(const double* uin, long long pitch, const BatchSeg* segs, int nprob,
+                                     long long maxn, const double* alpha, double gamma, int* arg, cudaStream_t st) {
+  return launch_adj_argmax_policy<StrictMath>(uin, pitch, segs, nprob, maxn, alpha, gamma, arg, st);
 }
 
 }  // namespace wt

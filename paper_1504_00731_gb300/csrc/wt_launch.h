@@ -90,6 +90,56 @@ cudaError_t launch_pack2d(const double* src, double* dst, long long nx, long lon
 cudaError_t launch_unpack2d(const double* src, double* dst, long long nx, long long ny, long long rowp,
                             long long planep, cudaStream_t st);
 
+// ---- discrete adjoint (1D Euler) -----------------------------------------------------
+struct AdjArgs {  // one reverse RK stage over a tile table
+  const double* uin;        // padded stage input planes [3][pitch]
+  long long pitch;
+  const BatchSeg* segs;     // uoff = offset of the problem in the [nprob][3][n] adjoint arrays, stride n
+  const int2* tiles;        // (problem, tile index), tile width T
+  int ntiles;
+  long long ustride;        // n: component stride of the adjoint arrays
+  const double* ubar_out;   // adjoint of the stage output
+  const double* alpha;      // [nprob][4]: alphas of the stage input
+  const double* dt;         // [nprob]
+  double cL;                // weight of dt L in the stage: 1, 1/4, 2/3
+  double gamma, eps, alpha_R;
+  const long long* goff;    // [nprob]: first interface slot of the problem in G (n + 1 slots)
+  double* G;                // [slots][36]: per interface, 6 cells x (fbar[3], Ubar[3])
+  double* partial;          // [ntiles][4]: d/d alpha_s (3) and d/d dt of the tile
+};
+
+struct GatherArgs {  // per-cell gather of the interface contributions
+  const double* uin;        // padded stage input planes (for the flux Jacobians)
+  long long pitch;
+  const BatchSeg* segs;
+  const long long* goff;
+  const double* G;
+  long long ustride;
+  const double* x;          // ubar_out
+  double* out;
+  double a_self;
+  int accumulate;
+  double* acc;              // may be null
+  double a_acc;
+  double gamma;
+};
+
+cudaError_t prepare_adj_strict();
+cudaError_t prepare_adj_fast();
+cudaError_t launch_adj_stage_strict(const AdjArgs& a, int grid, cudaStream_t st);
+cudaError_t launch_adj_stage_fast(const AdjArgs& a, int grid, cudaStream_t st);
+cudaError_t launch_adj_argmax_strict(const double* uin, long long pitch, const BatchSeg* segs, int nprob,
+                                     long long maxn, const double* alpha, double gamma, int* arg, cudaStream_t st);
+cudaError_t launch_adj_argmax_fast(const double* uin, long long pitch, const BatchSeg* segs, int nprob, long long maxn,
+                                   const double* alpha, double gamma, int* arg, cudaStream_t st);
+cudaError_t launch_adj_gather(const GatherArgs& a, int nprob, long long maxn, cudaStream_t st);
+cudaError_t launch_adj_apply(const double* uin, long long pitch, const BatchSeg* segs, const int* tstart,
+                             const int* tcount, const double* partial, const double* alpha, const double* dt,
+                             const int* arg, double* ubar, long long ustride, double* dtbar, int final_stage,
+                             double gamma, int nprob, cudaStream_t st);
+cudaError_t launch_adj_record(const Ctl* ctl, int slot, double* alpha_out, double* dt_out, int nprob, cudaStream_t st);
+int adj_tile_width();
+
 // Records a message for wt_last_error() on the calling thread and returns code.
 int set_last_error(int code, const char* msg);
 

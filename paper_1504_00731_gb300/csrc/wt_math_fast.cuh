@@ -19,6 +19,8 @@ namespace wt {
 
 struct FastMath {
   static constexpr bool kStrict = false;
+  // projection v = kProj (L f +- alpha L u) with the stored L = kLScale * L_true
+  static constexpr double kProj = 1.0, kLScale = 0.5;
 
   __device__ __forceinline__ static long long bits(double x) { return __double_as_longlong(x); }
   // max / min / less-than of non-negative doubles through their bit patterns
@@ -94,7 +96,8 @@ struct FastMath {
     vm = fma(-alpha, hu, 0.5 * f);
   }
 
-  __device__ __forceinline__ static double weno(const double* q, double eps, double alpha_R) {
+  __device__ __forceinline__ static double weno_flags(const double* q, double eps, double alpha_R, bool& restricted_out,
+                                                    bool& theta1_out) {
     constexpr double C1312 = 13.0 / 12.0, C1348 = 13.0 / 48.0;
     const double d0 = q[1] - q[0], d1 = q[2] - q[1], d2 = q[3] - q[2], d3 = q[4] - q[3], d4 = q[5] - q[4];
     const double s0 = d1 - d0, s1 = d2 - d1, s2 = d3 - d2, s3 = d4 - d3;
@@ -130,6 +133,8 @@ struct FastMath {
     const double bmax = nmax(nmax(b0, b1), nmax(b2, b3));
     const double bmin = nmin(nmin(b0, b1), nmin(b2, b3));
     const bool restricted = !(bits(fma(alpha_R, bmin, alpha_R * eps)) < bits(bmax));
+    restricted_out = restricted;
+    theta1_out = theta1;
     if (restricted) return fma(g3w, fh3, fma(g2, fh2, fma(g1, fh1, g0 * fh0)));
     // Eq. (om) over the common denominator prod_l (eps + beta_l)
     const double e0d = eps + b0, e1d = eps + b1, e2d = eps + b2, e3d = eps + b3;
@@ -140,6 +145,11 @@ struct FastMath {
     const double w3 = g3w * (e3d + tau) * (p01 * e2d);
     const double num = fma(w3, fh3, fma(w2, fh2, fma(w1, fh1, w0 * fh0)));
     return num / ((w0 + w1) + (w2 + w3));
+  }
+
+  __device__ __forceinline__ static double weno(const double* q, double eps, double alpha_R) {
+    bool r, t;
+    return weno_flags(q, eps, alpha_R, r, t);
   }
 
   __device__ __forceinline__ static void backproject(const double* rs, const double* F, double* h) {

@@ -10,6 +10,8 @@ namespace wt {
 
 struct StrictMath {
   static constexpr bool kStrict = true;
+  // projection v = kProj (L f +- alpha L u) with the stored L = kLScale * L_true
+  static constexpr double kProj = 0.5, kLScale = 1.0;
 
   // ---- scalar fluxes (Eq. (lin_eq), Eq. (bur_eq))
   __device__ __forceinline__ static double flux_advection(double a, double u) { return a * u; }
@@ -81,7 +83,8 @@ struct StrictMath {
 
   // ---- WENO-theta interface value, Eqs. (fh0)-(fh3), (be0_cen)-(be3_cen), (be_res),
   //      (tau_5), (tau_6), (tau_we6), (gam_we6), (om), (fh_nonlinear); q[i] at x_{j-2+i}
-  __device__ __forceinline__ static double weno(const double* q, double eps, double alpha_R) {
+  __device__ __forceinline__ static double weno_flags(const double* q, double eps, double alpha_R, bool& restricted,
+                                                    bool& theta1) {
     double fh0 = (2.0 * q[0] - 7.0 * q[1] + 11.0 * q[2]) / 6.0;
     double fh1 = (-q[1] + 5.0 * q[2] + 2.0 * q[3]) / 6.0;
     double fh2 = (2.0 * q[2] + 5.0 * q[3] - q[4]) / 6.0;
@@ -114,6 +117,8 @@ struct StrictMath {
     bmin = (b2 < bmin) ? b2 : bmin;
     bmin = (b3 < bmin) ? b3 : bmin;
     double ratio = bmax / (eps + bmin);
+    restricted = ratio <= alpha_R;
+    theta1 = !(tau6 < tau5);
     if (ratio <= alpha_R) {
       b0 = 0.0;
       b1 = 0.0;
@@ -141,6 +146,11 @@ struct StrictMath {
     double asum = a0 + a1 + a2 + a3;
     double w0 = a0 / asum, w1 = a1 / asum, w2 = a2 / asum, w3 = a3 / asum;
     return w0 * fh0 + w1 * fh1 + w2 * fh2 + w3 * fh3;
+  }
+
+  __device__ __forceinline__ static double weno(const double* q, double eps, double alpha_R) {
+    bool r, t;
+    return weno_flags(q, eps, alpha_R, r, t);
   }
 
   // ---- back-projection h = R (F+ + F-) with R = [r_1 r_2 r_3] of Roe's matrix

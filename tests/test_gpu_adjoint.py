@@ -1,0 +1,127 @@
+"""Discrete adjoint of the 1D Euler RK3 + WENO-theta map.
+
+Loss J = (dx / 2) sum_p sum_j (rho_pj(T) - rho*_pj)^2, so dJ/du(T) = dx (rho(T) - rho*) in the
+density component.  The adjoint gradient g must satisfy <g, d> = dJ(u0)[d] for every
+direction d, where dJ[d] is
+  - the oracle's forward-mode (dual-number) derivative of exactly the same map, with the same
+    frozen branches and first-index argmax convention (strict mode, any data), and
+  - a central finite difference (h = 1e-6) on smooth data whose maxima are attained at single
+    cells (no switching threshold within the difference step).
+"""
+import numpy as np
+import pytest
+
+from paper_1504_00731_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _gpu_adjoint(b, prob, g, U0, target, n_steps, K, cfl=0.5):
+    nprob, m, n = U0.shape
+    dx = (g.hi[0] - g.lo[0]) / n
+    ws = b.alloc_workspace(b.adjoint_workspace_bytes(prob, g, nprob, n_steps, K))
+    u0 = torch.from_numpy(np.ascontiguousarray(U0)).cuda()
+    # forward once for u(T) to build dJ/du(T)
+    uT = torch.empty_like(u0)
+    gT = torch.zeros_like(u0)
+    g0 = torch.empty_like(u0)
+    b.weno_theta_adjoint(prob, g, nprob, u0, cfl, n_steps, K, gT, g0, ws, uT=uT)
+    gT[:, 0, :] = dx * (uT[:, 0, :] - torch.from_numpy(target).cuda())
+    b.weno_theta_adjoint(prob, g, nprob, u0, cfl, n_steps, K, gT, g0, ws, uT=uT)
+    torch.cuda.synchronize()
+    return g0.cpu().numpy(), uT.cpu().numpy()
+
+
+def _smooth_states(nprob, n, seed):
+    rng = np.random.default_rng(seed)
+    x, dx = W.grid_1d(n, -1.0, 1.0, periodic=True)
+    out = np.empty((nprob, 3, n))
+    for p in range(nprob):
+        a = rng.uniform(0.05, 0.2, 3)
+        ph = rng.uniform(0, 2 * np.pi, 3)
+        rho = 1.0 + a[0] * np.sin(np.pi * x + ph[0])
+        u = 0.3 + a[1] * np.sin(np.pi * x + ph[1])
+        p_ = 1.0 + a[2] * np.cos(np.pi * x + ph[2])
+        out[p] = W.cons_1d(rho, u, p_)
+    return out, dx
+
+
+def _riemann_states(nprob, n, seed, periodic=False):
+    out = np.empty((nprob, 3, n))
+    for p in range(nprob):
+        U, x, dx = W.euler_riemann(n, W.riemann_params(seed * 101 + p), periodic=periodic)
+        out[p] = U
+    return out, dx
+
+
+@pytest.mark.parametrize("bc,periodic", [(1, False), (0, True)], ids=["outflow", "periodic"])
+def test_adjoint_strict_matches_dual_numbers(wtlib, oracle, bc, periodic):
+    """Riemann + entropy-wave data (constant states, so exact ties in the maxima), 11 steps with
+    checkpoints every 4 (segments of 4, 4, 3)."""
+    b, O = wtlib, oracle
+    nprob, n, steps, K = 2, 64, 11, 4
+    U0, dx = _riemann_states(nprob, n, seed=3, periodic=periodic)
+    rng = np.random.default_rng(0)
+    target = U0[:, 0, :] * (1 + 0.05 * rng.standard_normal((nprob, n)))
+    prob = b.problem(b.WT_FLUX_EULER1D, bc=bc, mode=b.WT_MODE_STRICT, alpha_R=W.ALPHA_R_SEEDED)
+    g = b.grid_1d(n, -5.0, 5.0)
+    g0, uT = _gpu_adjoint(b, prob, g, U0, target, steps, K)
+    P = O.problem(O.FLUX_EULER1D, bc=bc, alpha_R=W.ALPHA_R_SEEDED)
+    for trial in range(4):
+        d = rng.standard_normal((nprob, 3, n))
+        dj = 0.0
+        for p in range(nprob):
+            uTp, duTp, _, _ = O.run_jvp(P, U0[p], d[p], dx, cfl=0.5, n_steps=steps)
+            assert np.array_equal(uTp, uT[p])
+            dj += dx * np.dot(uTp[0] - target[p], duTp[0])
+        adj = float(np.sum(g0 * d))
+        assert abs(adj - dj) <= 1e-9 * max(abs(dj), 1e-30), (adj, dj)
+
+
+def test_adjoint_fast_matches_finite_differences(wtlib):
+    """Smooth periodic data (single-cell maxima), fast mode, 24 steps, checkpoints every 7."""
+    b = wtlib
+    nprob, n, steps, K = 3, 96, 24, 7
+    U0, dx = _smooth_states(nprob, n, seed=5)
+    rng = np.random.default_rng(1)
+    target = U0[:, 0, :] + 0.02 * rng.standard_normal((nprob, n))
+    prob = b.problem(b.WT_FLUX_EULER1D, bc=b.WT_BC_PERIODIC, mode=b.WT_MODE_FAST)
+    g = b.grid_1d(n, -1.0, 1.0)
+    g0, _ = _gpu_adjoint(b, prob, g, U0, target, steps, K)
+    segs = []
+    for p in range(nprob):
+        s = b.WtSegment()
+        s.offset, s.n, s.lo, s.hi, s.bc_lo, s.bc_hi = p * n, n, -1.0, 1.0, 0, 0
+        segs.append(s)
+    ws = b.alloc_workspace(b.workspace_bytes(prob, None, nprob * n, nprob))
+
+    def J(U):
+        packed = np.ascontiguousarray(np.concatenate([U[p] for p in range(nprob)], axis=1))
+        u = torch.from_numpy(packed).cuda()
+        b.weno_theta_step_batched(prob, segs, u, nprob * n, 0.5, steps, ws)
+        rho = u.cpu().numpy()[0].reshape(nprob, n)
+        return 0.5 * dx * np.sum((rho - target) ** 2)
+
+    h = 1e-6
+    for trial in range(4):
+        x, _ = W.grid_1d(n, -1.0, 1.0, periodic=True)
+        d = np.stack([np.stack([rng.uniform(0.5, 1) * np.sin(np.pi * x + rng.uniform(0, 6.3)) for _ in range(3)])
+                      for _ in range(nprob)])
+        fd = (J(U0 + h * d) - J(U0 - h * d)) / (2 * h)
+        adj = float(np.sum(g0 * d))
+        assert abs(adj - fd) <= 1e-6 * abs(fd), (adj, fd)
+
+
+def test_adjoint_returns_the_forward_state(wtlib):
+    b = wtlib
+    nprob, n, steps = 3, 200, 9
+    U0, dx = _riemann_states(nprob, n, seed=8)
+    prob = b.problem(b.WT_FLUX_EULER1D, bc=b.WT_BC_OUTFLOW, alpha_R=W.ALPHA_R_SEEDED)
+    g = b.grid_1d(n, -5.0, 5.0)
+    _, uT = _gpu_adjoint(b, prob, g, U0, U0[:, 0, :], steps, 4)
+    for p in range(nprob):
+        ws = b.alloc_workspace(b.workspace_bytes(prob, g))
+        u = torch.from_numpy(np.ascontiguousarray(U0[p])).cuda()
+        b.weno_theta_step(prob, g, u, 0.5, ws, max_steps=steps)
+        assert np.array_equal(u.cpu().numpy(), uT[p])
