@@ -27,15 +27,30 @@ namespace wt {
 // ---------------------------------------------------------------------------------------
 
 // qbar += Fbar * dF/dq for the WENO-theta value F(q) of Eqs. (fh_nonlinear)-(tau_we6), with the
-// restriction of Eq. (be_res) and the theta of Eq. (tau_we6) frozen as given.
+// restriction of Eq. (be_res) and the theta of Eq. (tau_we6) frozen as given.  A restricted
+// stencil has every alpha_k scaled by the same factor 1 + tau/eps, so its weights are the
+// linear gamma^theta and dF/dq is the coefficient vector of Eq. (fh_5) (theta = 1) or
+// Eq. (fh_6) (theta = 0).
 __device__ __forceinline__ void weno_grad(const double* q, double eps, bool restricted, bool theta1, double Fbar,
                                           double* qbar) {
+  if (restricted) {
+    if (theta1) {
+      constexpr double c5[6] = {2.0 / 60, -13.0 / 60, 47.0 / 60, 27.0 / 60, -3.0 / 60, 0.0};
+#pragma unroll
+      for (int i = 0; i < 5; ++i) qbar[i] = fma(c5[i], Fbar, qbar[i]);
+    } else {
+      constexpr double c6[6] = {1.0 / 60, -8.0 / 60, 37.0 / 60, 37.0 / 60, -8.0 / 60, 1.0 / 60};
+#pragma unroll
+      for (int i = 0; i < 6; ++i) qbar[i] = fma(c6[i], Fbar, qbar[i]);
+    }
+    return;
+  }
   constexpr double C12 = 13.0 / 12.0, C48 = 13.0 / 48.0;
   constexpr double cfh[4][6] = {{2.0 / 6, -7.0 / 6, 11.0 / 6, 0, 0, 0},
                                 {0, -1.0 / 6, 5.0 / 6, 2.0 / 6, 0, 0},
                                 {0, 0, 2.0 / 6, 5.0 / 6, -1.0 / 6, 0},
                                 {0, 0, 0, 11.0 / 6, -7.0 / 6, 2.0 / 6}};
-  // beta_k = c_k x_k^2 + y_k^2 with x_k = vx_k . q, y_k = vy_k . q
+  // beta_k = cb_k x_k^2 + y_k^2 with x_k = vx_k . q, y_k = vy_k . q
   constexpr double vx[4][6] = {{1, -2, 1, 0, 0, 0}, {0, 1, -2, 1, 0, 0}, {0, 0, 1, -2, 1, 0}, {0, 0, 3, -7, 5, -1}};
   constexpr double vy[4][6] = {{1, -3, 2, 0, 0, 0}, {0, 0, -1, 1, 0, 0}, {0, 0, 1, -1, 0, 0}, {0, 0, 0, 2, -3, 1}};
   constexpr double cb[4] = {C12, C12, C12, C48};
@@ -47,55 +62,69 @@ __device__ __forceinline__ void weno_grad(const double* q, double eps, bool rest
     double f = 0, x = 0, y = 0;
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
-      f += cfh[k][i] * q[i];
-      x += vx[k][i] * q[i];
-      y += vy[k][i] * q[i];
+      if (cfh[k][i] != 0.0) f = fma(cfh[k][i], q[i], f);
+      if (vx[k][i] != 0.0) x = fma(vx[k][i], q[i], x);
+      if (vy[k][i] != 0.0) y = fma(vy[k][i], q[i], y);
     }
     fh[k] = f;
     xb[k] = x;
     yb[k] = y;
-    beta[k] = cb[k] * x * x + y * y;
+    beta[k] = fma(cb[k] * x, x, y * y);
   }
-  double x5 = 0, y5 = 0, x6 = 0, y6 = 0;
+  double xt = 0, yt = 0;
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
-    x5 += v5x[i] * q[i];
-    y5 += v5y[i] * q[i];
-    x6 += v6x[i] * q[i];
-    y6 += v6y[i] * q[i];
+    if (theta1) {
+      if (v5x[i] != 0.0) xt = fma(v5x[i], q[i], xt);
+      if (v5y[i] != 0.0) yt = fma(v5y[i], q[i], yt);
+    } else {
+      if (v6x[i] != 0.0) xt = fma(v6x[i], q[i], xt);
+      if (v6y[i] != 0.0) yt = fma(v6y[i], q[i], yt);
+    }
   }
-  const double tau = theta1 ? (C12 * x5 * x5 + y5 * y5) : (C12 * x6 * x6 + 0.25 * y6 * y6);
+  const double tau = theta1 ? fma(C12 * xt, xt, yt * yt) : fma(C12 * xt, xt, 0.25 * yt * yt);
   const double g[4] = {theta1 ? 2.0 / 20.0 : 1.0 / 20.0, theta1 ? 12.0 / 20.0 : 9.0 / 20.0,
                        theta1 ? 6.0 / 20.0 : 9.0 / 20.0, theta1 ? 0.0 : 1.0 / 20.0};
-  double d[4], a[4], S = 0;
+  double d[4], id[4], a[4], S = 0;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    d[k] = eps + (restricted ? 0.0 : beta[k]);
-    a[k] = g[k] * (1.0 + tau / d[k]);
+    d[k] = eps + beta[k];
+    id[k] = 1.0 / d[k];
+    a[k] = g[k] * fma(tau, id[k], 1.0);
     S += a[k];
   }
+  const double iS = 1.0 / S;
   double F = 0;
 #pragma unroll
-  for (int k = 0; k < 4; ++k) F += (a[k] / S) * fh[k];
-  double taub = 0;
-  double bb[4];
+  for (int k = 0; k < 4; ++k) F = fma(a[k] * iS, fh[k], F);
+  double taub = 0, fhb[4], xbb[4], ybb[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    const double ab = Fbar * (fh[k] - F) / S;  // adjoint of a_k
-    taub += ab * g[k] / d[k];
-    bb[k] = restricted ? 0.0 : -ab * g[k] * tau / (d[k] * d[k]);
+    const double ab = Fbar * (fh[k] - F) * iS;  // adjoint of a_k
+    taub = fma(ab * g[k], id[k], taub);
+    const double bbk = -ab * g[k] * tau * id[k] * id[k];  // adjoint of beta_k
+    xbb[k] = 2.0 * cb[k] * xb[k] * bbk;
+    ybb[k] = 2.0 * yb[k] * bbk;
+    fhb[k] = Fbar * a[k] * iS;
   }
+  const double xtb = 2.0 * C12 * xt * taub, ytb = (theta1 ? 2.0 : 0.5) * yt * taub;
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
-    double s = 0;
+    double s = qbar[i];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      s += Fbar * (a[k] / S) * cfh[k][i];
-      s += bb[k] * (2.0 * cb[k] * xb[k] * vx[k][i] + 2.0 * yb[k] * vy[k][i]);
+      if (cfh[k][i] != 0.0) s = fma(cfh[k][i], fhb[k], s);
+      if (vx[k][i] != 0.0) s = fma(vx[k][i], xbb[k], s);
+      if (vy[k][i] != 0.0) s = fma(vy[k][i], ybb[k], s);
     }
-    s += theta1 ? taub * (2.0 * C12 * x5 * v5x[i] + 2.0 * y5 * v5y[i])
-                : taub * (2.0 * C12 * x6 * v6x[i] + 0.5 * y6 * v6y[i]);
-    qbar[i] += s;
+    if (theta1) {
+      if (v5x[i] != 0.0) s = fma(v5x[i], xtb, s);
+      if (v5y[i] != 0.0) s = fma(v5y[i], ytb, s);
+    } else {
+      if (v6x[i] != 0.0) s = fma(v6x[i], xtb, s);
+      if (v6y[i] != 0.0) s = fma(v6y[i], ytb, s);
+    }
+    qbar[i] = s;
   }
 }
 
@@ -306,7 +335,18 @@ __global__ void __launch_bounds__(AdjTile<T>::NT) adj_stage_kernel(const AdjArgs
       for (int e = 0; e < 3; ++e) s_rs[e * NI + i] = rs[e];
     }
     __syncthreads();
-    // ---- C1 forward: F_s per interface and field; hbar per interface
+    // ---- hbar per interface: L_gi and L_gi+1 depend on h of interface gi = j0 - 1 + i
+    for (int k = tid; k < 3 * ni; k += NT) {
+      const int c = k / ni, i = k - c * ni;
+      const long long gi = j0 - 1 + i;
+      const double wl = (gi >= 0) ? s_w[c * (T + 2) + i] : 0.0;
+      const double wr = (gi + 1 < n) ? s_w[c * (T + 2) + i + 1] : 0.0;
+      s_hb[c * NI + i] = (wr - wl) / sg.dx;
+    }
+    __syncthreads();
+    // ---- C1: per (interface, field), one pass: projection, both reconstructions with the
+    //      forward policy's branches, F_s; then their reverse (owned interfaces only)
+    double abar0 = 0.0, abar1 = 0.0, abar2 = 0.0;
     for (int item2 = tid; item2 < 3 * ni; item2 += NT) {
       const int s = item2 / ni, i = item2 - s * ni;
       const double l[3] = {s_L[(3 * s) * NI + i], s_L[(3 * s + 1) * NI + i], s_L[(3 * s + 2) * NI + i]};
@@ -320,15 +360,50 @@ __global__ void __launch_bounds__(AdjTile<T>::NT) adj_stage_kernel(const AdjArgs
       }
 #pragma unroll
       for (int kk = 0; kk < 6; ++kk) qm[kk] = vm[5 - kk];
-      s_F[s * NI + i] = MATH::weno(vp, a.eps, a.alpha_R) + MATH::weno(qm, a.eps, a.alpha_R);
-      // hbar of global interface gi = j0 - 1 + i: L_gi and L_gi+1 depend on it
-      const long long gi = j0 - 1 + i;
-      const double wl = (gi >= 0) ? s_w[s * (T + 2) + i] : 0.0;
-      const double wr = (gi + 1 < n) ? s_w[s * (T + 2) + i + 1] : 0.0;
-      s_hb[s * NI + i] = (wr - wl) / sg.dx;  // here s indexes the component
+      bool rp, tp, rm, tm;
+      const double Fs = MATH::weno_flags(vp, a.eps, a.alpha_R, rp, tp) + MATH::weno_flags(qm, a.eps, a.alpha_R, rm, tm);
+      s_F[s * NI + i] = Fs;
+      const bool owned = (i >= 1) || (j0 == 0);
+      if (!owned) continue;
+      double* Gs = s_G + (s * NI + i) * 36;
+      double* Lbs = s_Lb + (s * NI + i) * 3;
+      const double u = s_rs[i], H = s_rs[NI + i], c = s_rs[2 * NI + i];
+      const double hb[3] = {s_hb[i], s_hb[NI + i], s_hb[2 * NI + i]};
+      // Fbar_s = sum_c R[c][s] hbar_c, R columns (1, u-c, H-uc), (1, u, u^2/2), (1, u+c, H+uc)
+      double Fb;
+      if (s == 0) Fb = hb[0] + (u - c) * hb[1] + (H - u * c) * hb[2];
+      else if (s == 1) Fb = hb[0] + u * hb[1] + 0.5 * u * u * hb[2];
+      else Fb = hb[0] + (u + c) * hb[1] + (H + u * c) * hb[2];
+      double vpb[6] = {0, 0, 0, 0, 0, 0}, qmb[6] = {0, 0, 0, 0, 0, 0};
+      weno_grad(vp, a.eps, rp, tp, Fb, vpb);
+      weno_grad(qm, a.eps, rm, tm, Fb, qmb);
+      double Lb3[3] = {0, 0, 0};
+      double ab_alpha = 0.0;
+#pragma unroll
+      for (int kk = 0; kk < 6; ++kk) {
+        const int k = i + kk;
+        const double f[3] = {s_f[k], s_f[W + k], s_f[2 * W + k]};
+        const double U[3] = {s_uin[off + k], s_uin[W + off + k], s_uin[2 * W + off + k]};
+        const double vmb = qmb[5 - kk];
+        const double bq = fma(l[2], U[2], fma(l[1], U[1], l[0] * U[0]));  // stored-L projection of u
+        const double abk = MATH::kProj * (vpb[kk] + vmb);
+        const double bbk = MATH::kProj * al[s] * (vpb[kk] - vmb);
+        ab_alpha = fma(MATH::kProj * bq, vpb[kk] - vmb, ab_alpha);
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+          Lb3[e] = fma(abk, f[e], fma(bbk, U[e], Lb3[e]));
+          Gs[kk * 6 + e] = abk * l[e];      // adjoint of the physical flux of stencil cell kk
+          Gs[kk * 6 + 3 + e] = bbk * l[e];  // adjoint of the state of stencil cell kk
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < 3; ++e) Lbs[e] = Lb3[e];
+      if (s == 0) abar0 += ab_alpha;
+      else if (s == 1) abar1 += ab_alpha;
+      else abar2 += ab_alpha;
     }
     __syncthreads();
-    // ---- D forward: h and the d/d dt partial  sum_j ubar_out_j . L_j (weighted by cL)
+    // ---- D forward: h per interface, and the d/d dt partial  cL sum_j ubar_out_j . L_j
     for (int i = tid; i < ni; i += NT) {
       const double rs[3] = {s_rs[i], s_rs[NI + i], s_rs[2 * NI + i]};
       const double F[3] = {s_F[i], s_F[NI + i], s_F[2 * NI + i]};
@@ -346,66 +421,6 @@ __global__ void __launch_bounds__(AdjTile<T>::NT) adj_stage_kernel(const AdjArgs
         dtb += a.cL * ubo[c * a.ustride + j0 + t] * L;
       }
     }
-    // ---- C1 reverse: per owned (interface, field)
-    double abar0 = 0.0, abar1 = 0.0, abar2 = 0.0;
-    for (int item2 = tid; item2 < 3 * ni; item2 += NT) {
-      const int s = item2 / ni, i = item2 - s * ni;
-      const bool owned = (i >= 1) || (j0 == 0);
-      double* Gs = s_G + (s * NI + i) * 36;
-      double* Lbs = s_Lb + (s * NI + i) * 3;
-      if (!owned) {
-        continue;
-      }
-      const double u = s_rs[i], H = s_rs[NI + i], c = s_rs[2 * NI + i];
-      const double hb[3] = {s_hb[i], s_hb[NI + i], s_hb[2 * NI + i]};
-      // Fbar_s = sum_c R[c][s] hbar_c, R columns (1, u-c, H-uc), (1, u, u^2/2), (1, u+c, H+uc)
-      double Fb;
-      if (s == 0) Fb = hb[0] + (u - c) * hb[1] + (H - u * c) * hb[2];
-      else if (s == 1) Fb = hb[0] + u * hb[1] + 0.5 * u * u * hb[2];
-      else Fb = hb[0] + (u + c) * hb[1] + (H + u * c) * hb[2];
-      const double l[3] = {s_L[(3 * s) * NI + i], s_L[(3 * s + 1) * NI + i], s_L[(3 * s + 2) * NI + i]};
-      double vp[6], vm[6], qm[6];
-#pragma unroll
-      for (int kk = 0; kk < 6; ++kk) {
-        const int k = i + kk;
-        const double f[3] = {s_f[k], s_f[W + k], s_f[2 * W + k]};
-        const double U[3] = {s_uin[off + k], s_uin[W + off + k], s_uin[2 * W + off + k]};
-        MATH::project3(l, f, U, al[s], vp[kk], vm[kk]);
-      }
-#pragma unroll
-      for (int kk = 0; kk < 6; ++kk) qm[kk] = vm[5 - kk];
-      bool rp, tp, rm, tm;
-      MATH::weno_flags(vp, a.eps, a.alpha_R, rp, tp);
-      MATH::weno_flags(qm, a.eps, a.alpha_R, rm, tm);
-      double vpb[6] = {0, 0, 0, 0, 0, 0}, qmb[6] = {0, 0, 0, 0, 0, 0};
-      weno_grad(vp, a.eps, rp, tp, Fb, vpb);
-      weno_grad(qm, a.eps, rm, tm, Fb, qmb);
-      double Lb3[3] = {0, 0, 0};
-      double ab_alpha = 0.0;
-#pragma unroll
-      for (int kk = 0; kk < 6; ++kk) {
-        const int k = i + kk;
-        const double f[3] = {s_f[k], s_f[W + k], s_f[2 * W + k]};
-        const double U[3] = {s_uin[off + k], s_uin[W + off + k], s_uin[2 * W + off + k]};
-        const double vmb = qmb[5 - kk];
-        const double bq = l[0] * U[0] + l[1] * U[1] + l[2] * U[2];  // stored-L projection of u
-        const double abk = MATH::kProj * (vpb[kk] + vmb);
-        const double bbk = MATH::kProj * al[s] * (vpb[kk] - vmb);
-        ab_alpha += MATH::kProj * bq * (vpb[kk] - vmb);
-#pragma unroll
-        for (int e = 0; e < 3; ++e) {
-          Lb3[e] += abk * f[e] + bbk * U[e];
-          Gs[kk * 6 + e] = abk * l[e];      // adjoint of the physical flux of stencil cell kk
-          Gs[kk * 6 + 3 + e] = bbk * l[e];  // adjoint of the state of stencil cell kk
-        }
-      }
-#pragma unroll
-      for (int e = 0; e < 3; ++e) Lbs[e] = Lb3[e];
-      if (s == 0) abar0 += ab_alpha;
-      else if (s == 1) abar1 += ab_alpha;
-      else abar2 += ab_alpha;
-    }
-    __syncthreads();
     // ---- D reverse: Roe's average per owned interface, fold the fields, write G
     for (int i = tid; i < ni; i += NT) {
       const bool owned = (i >= 1) || (j0 == 0);
@@ -612,10 +627,19 @@ __global__ void adj_record_kernel(const Ctl* ctl, int slot, double* alpha_out, d
 
 #endif  // WT_ADJOINT_COMMON_KERNELS
 
+// grid <= 0: as many CTAs as can be resident (persistent loop over the tile table)
 template <class MATH>
 cudaError_t launch_adj_stage_policy(const AdjArgs& a, int grid, cudaStream_t st) {
   constexpr int T = 31;
   using TL = AdjTile<T>;
+  if (grid <= 0) {
+    int dev = 0, sms = 0, nb = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, adj_stage_kernel<MATH, T>, TL::NT, TL::bytes);
+    long long g = (long long)(nb > 0 ? nb : 1) * (sms > 0 ? sms : 1);
+    grid = (int)(g < a.ntiles ? g : a.ntiles);
+  }
   adj_stage_kernel<MATH, T><<<grid, TL::NT, TL::bytes, st>>>(a);
   return cudaGetLastError();
 }

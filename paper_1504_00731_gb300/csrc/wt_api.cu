@@ -1156,6 +1156,7 @@ int weno_theta_adjoint(const wt_problem* prob, const wt_grid* grid, int32_t npro
     return b;
   };
   const int nf = (int)tf.size(), nr = (int)tr.size();
+  (void)nr;
   const int grid_f = batched_grid_size(prob, 127, nf, dev);
 
   // ---- forward pass with checkpoints
@@ -1193,10 +1194,7 @@ int weno_theta_adjoint(const wt_problem* prob, const wt_grid* grid, int32_t npro
     WT_CUDA(cudaMemcpyAsync(vX, dJ_duT, vec_bytes, cudaMemcpyHostToDevice, st));
   }
   WT_CUDA(cudaMemsetAsync(dtbar, 0, sizeof(double) * nprob, st));
-  int occ = 0, sms = 0;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  occ = 2;
-  const int grid_r = std::min(nr, occ * sms);
+  const int grid_r = 0;  // resident-CTA count from the occupancy calculator
   for (int64_t sg = S - 1; sg >= 0; --sg) {
     const int64_t kseg = std::min<int64_t>(K, n_steps - sg * K);
     // recompute the segment, keeping u^n, u^(1), u^(2) of every step and their alphas and dt
