@@ -45,6 +45,8 @@ FLOPS_PER_CELL_UPDATE = 3696.0
 BYTES_PER_CELL_UPDATE = 64.0 * M
 # FP64 peak from unit counts: 152 SMs x 2 FP64 FMA lanes per clock x 2 flops x 2.07 GHz.
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
+# 2D Euler flops per cell-update, counted the same way (oracle operation counter, 64^2 state)
+FLOPS_PER_CELL_UPDATE_2D = 10449.0
 L2_FLUSH_BYTES = 256 << 20
 KERNEL_SOURCES = ("wt_kernels.cuh", "wt_math_fast.cuh", "wt_device.cuh")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "stage1d_euler_N4096_traffic.json")
@@ -219,6 +221,81 @@ def batched_measure(B, dev, steps=20, plain_sample=64):
             "workload": "4096 x 1D Euler, N log-uniform in [256, 65536], mixed periodic/outflow, CFL 0.5"}
 
 
+def euler2d_measure(B, dev, steps=5):
+    """2D Euler, 4096 x 4096 periodic vortex / quadrant state, CFL 0.45, timed over `steps` RK
+    steps of the 500-step workload (throughput per step does not depend on the count)."""
+    import torch
+
+    n = 4096
+    U, dx, dy = W.euler2d_vortices(n, n, seed=0)
+    prob = B.problem(B.WT_FLUX_EULER2D, bc=B.WT_BC_PERIODIC, mode=B.WT_MODE_FAST, alpha_R=W.ALPHA_R_SEEDED)
+    g = B.grid_2d(n, n)
+    ws = B.alloc_workspace(B.workspace_bytes(prob, g), dev)
+    u0 = torch.from_numpy(U).to(dev)
+    u = u0.clone()
+    B.weno_theta_step(prob, g, u, 0.45, ws, max_steps=1)
+    u.copy_(u0)
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    B.weno_theta_step(prob, g, u, 0.45, ws, max_steps=steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) * 1e-3
+    v = n * n * steps / t
+    return {"value": v, "unit": "cell-updates/s", "cells": n * n, "rk_steps_timed": steps,
+            "flops_per_cell_update": FLOPS_PER_CELL_UPDATE_2D,
+            "roofline_frac_alu": v * FLOPS_PER_CELL_UPDATE_2D / 1e9 / FP64_PEAK_GFLOPS,
+            "workload": "2D Euler 4096^2 periodic, 4 quadrants + 8 isentropic vortices, CFL 0.45"}
+
+
+def adjoint_measure(B, dev, nprob=256, n=16384, steps=64, K=32):
+    """Discrete adjoint of nprob x n 1D Euler cells through `steps` RK steps with checkpoints every
+    K (the adjoint workload runs 1024 steps with K = 32), against one plain forward run of the
+    same problems through the batched entry point."""
+    import torch
+
+    U0 = np.empty((nprob, 3, n))
+    for p in range(nprob):
+        U0[p] = W.euler_riemann(n, W.riemann_params(p))[0]
+    prob = B.problem(B.WT_FLUX_EULER1D, bc=B.WT_BC_OUTFLOW, mode=B.WT_MODE_FAST, alpha_R=W.ALPHA_R_SEEDED)
+    g = B.grid_1d(n, -5.0, 5.0)
+    ws = B.alloc_workspace(B.adjoint_workspace_bytes(prob, g, nprob, steps, K), dev)
+    u0 = torch.from_numpy(U0).to(dev)
+    uT, gT, g0 = torch.empty_like(u0), torch.zeros_like(u0), torch.empty_like(u0)
+    gT[:, 0, :] = 1e-3
+    B.weno_theta_adjoint(prob, g, nprob, u0, 0.5, 2, 2, gT, g0, ws, uT=uT)
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    B.weno_theta_adjoint(prob, g, nprob, u0, 0.5, steps, K, gT, g0, ws, uT=uT)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_adj = e0.elapsed_time(e1) * 1e-3
+    del ws
+    segs = []
+    for p in range(nprob):
+        s = B.WtSegment()
+        s.offset, s.n, s.lo, s.hi, s.bc_lo, s.bc_hi = p * n, n, -5.0, 5.0, 1, 1
+        segs.append(s)
+    wsb = B.alloc_workspace(B.workspace_bytes(prob, None, nprob * n, nprob), dev)
+    packed = u0.permute(1, 0, 2).reshape(3, nprob * n).contiguous()
+    u = packed.clone()
+    B.weno_theta_step_batched(prob, segs, u, nprob * n, 0.5, 2, wsb)
+    u = packed.clone()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    B.weno_theta_step_batched(prob, segs, u, nprob * n, 0.5, steps, wsb)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_fwd = e0.elapsed_time(e1) * 1e-3
+    return {"adjoint_over_forward": t_adj / t_fwd, "adjoint_s": t_adj, "forward_s": t_fwd, "problems": nprob,
+            "n": n, "rk_steps": steps, "checkpoint_every": K, "grad_finite": bool(torch.isfinite(g0).all()),
+            "workload": "256 x 1D Euler N=16384 (seeded Riemann + entropy wave), outflow, CFL 0.5"}
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -366,6 +443,8 @@ def run_ours(args):
         }
         if world == 1 and not args.no_extras:
             line["batched"] = batched_measure(B, dev)
+            line["euler2d"] = euler2d_measure(B, dev)
+            line["adjoint"] = adjoint_measure(B, dev)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)
