@@ -219,7 +219,7 @@ int stage_in(const double* u, bool u_dev, double* staging, int m, long long n, l
 // --- CUDA graph of one RK step (three fused stage launches), cached per argument set
 struct GraphEntry {
   Stage1DArgs a[3];
-  int flux, mode, tile, device;
+  int flux, mode, tile, device, nsteps;
   cudaGraphExec_t exec;
 };
 std::mutex g_graph_mu;
@@ -228,11 +228,12 @@ cudaStream_t g_capture_stream[64] = {};
 
 bool same_args(const Stage1DArgs& x, const Stage1DArgs& y) { return memcmp(&x, &y, sizeof x) == 0; }
 
-int get_step_graph(const wt_problem* p, int device, int tile, const Stage1DArgs a[3], cudaGraphExec_t* out) {
+int get_step_graph(const wt_problem* p, int device, int tile, int nsteps, const Stage1DArgs a[3],
+                   cudaGraphExec_t* out) {
   std::lock_guard<std::mutex> lk(g_graph_mu);
   for (auto& e : g_graphs) {
-    if (e.device == device && e.flux == p->flux && e.mode == p->mode && e.tile == tile && same_args(e.a[0], a[0]) &&
-        same_args(e.a[1], a[1]) && same_args(e.a[2], a[2])) {
+    if (e.device == device && e.flux == p->flux && e.mode == p->mode && e.tile == tile && e.nsteps == nsteps &&
+        same_args(e.a[0], a[0]) && same_args(e.a[1], a[1]) && same_args(e.a[2], a[2])) {
       *out = e.exec;
       return WT_OK;
     }
@@ -242,7 +243,8 @@ int get_step_graph(const wt_problem* p, int device, int tile, const Stage1DArgs 
   if (!cs) WT_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
   WT_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
   cudaError_t le = cudaSuccess;
-  for (int s = 0; s < 3 && le == cudaSuccess; ++s) le = launch_stage(p, s, tile, a[s], cs);
+  for (int k = 0; k < nsteps; ++k)
+    for (int s = 0; s < 3 && le == cudaSuccess; ++s) le = launch_stage(p, s, tile, a[s], cs);
   cudaGraph_t graph = nullptr;
   cudaError_t ee = cudaStreamEndCapture(cs, &graph);
   if (le != cudaSuccess) return fail(WT_ERR_CUDA, "stage launch during capture: %s", cudaGetErrorString(le));
@@ -263,6 +265,7 @@ int get_step_graph(const wt_problem* p, int device, int tile, const Stage1DArgs 
   e.mode = p->mode;
   e.tile = tile;
   e.device = device;
+  e.nsteps = nsteps;
   e.exec = exec;
   g_graphs.push_back(e);
   *out = exec;
@@ -815,8 +818,12 @@ int weno_theta_step(const wt_problem* prob, const wt_grid* grid, double* u, doub
   a[2].uin = U2;
   a[2].un = Un;
   a[2].uout = Un;
-  cudaGraphExec_t exec;
-  if (max_steps > 0 && (rc = get_step_graph(prob, dev, tile, a, &exec)) != WT_OK) return rc;
+  // RK steps replay from graphs of kGraphSteps steps (programmatic edges between their stage
+  // launches) plus a one-step graph for the remainder
+  constexpr int kGraphSteps = 8;
+  cudaGraphExec_t exec1 = nullptr, execK = nullptr;
+  if (max_steps > 0 && (rc = get_step_graph(prob, dev, tile, 1, a, &exec1)) != WT_OK) return rc;
+  if (max_steps >= kGraphSteps && (rc = get_step_graph(prob, dev, tile, kGraphSteps, a, &execK)) != WT_OK) return rc;
 
   Ctl hc;
   int64_t launched = 0;
@@ -825,7 +832,9 @@ int weno_theta_step(const wt_problem* prob, const wt_grid* grid, double* u, doub
   while (launched < max_steps) {
     int64_t k = max_steps - launched;
     if (k > chunk) k = chunk;
-    for (int64_t i = 0; i < k; ++i) WT_CUDA(cudaGraphLaunch(exec, st));
+    int64_t i = 0;
+    for (; execK && i + kGraphSteps <= k; i += kGraphSteps) WT_CUDA(cudaGraphLaunch(execK, st));
+    for (; i < k; ++i) WT_CUDA(cudaGraphLaunch(exec1, st));
     launched += k;
     if (bounded_time) {
       WT_CUDA(cudaMemcpyAsync(&hc, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));

@@ -39,6 +39,12 @@ __device__ __forceinline__ void flag_error(Ctl* ctl, int code) {
 // on through it (the sound speed there is NaN and drops out of the alpha maxima).
 __device__ __forceinline__ bool finite3(const double* U) { return isfinite(U[0]) && isfinite(U[1]) && isfinite(U[2]); }
 
+// Programmatic dependent launch: let the next kernel in the stream start its prologue now,
+// and wait (in hardware) until the previous kernel has completed and its writes are visible.
+// Both are no-ops for a kernel launched without the programmatic-serialization attribute.
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // ---------------------------------------------------------------------------------------
 // Bulk copies global -> shared (cp.async.bulk, completion on an mbarrier)
 // ---------------------------------------------------------------------------------------

@@ -337,8 +337,10 @@ template <class MATH, int FLUX, int STAGE, int T>
 __global__ void __launch_bounds__(Tile1D<T, FluxM<FLUX>::m>::NT) stage1d_kernel(const Stage1DArgs a) {
   using TL = Tile1D<T, FluxM<FLUX>::m>;
   extern __shared__ __align__(16) double sm[];
+  pdl_launch_dependents();
   if (threadIdx.x == 0) mbar_init(reinterpret_cast<uint64_t*>(sm + TL::kBar), 1);
   __syncthreads();
+  pdl_wait();
   uint32_t phase = 0;
   stage1d_tile<MATH, FLUX, STAGE, T>(a, (long long)blockIdx.x * T, blockIdx.x == 0, sm, phase);
 }
@@ -349,8 +351,10 @@ template <class MATH, int FLUX, int STAGE, int T>
 __global__ void __launch_bounds__(Tile1D<T, FluxM<FLUX>::m>::NT) stage1d_batched_kernel(const BatchArgs b) {
   using TL = Tile1D<T, FluxM<FLUX>::m>;
   extern __shared__ __align__(16) double sm[];
+  pdl_launch_dependents();
   if (threadIdx.x == 0) mbar_init(reinterpret_cast<uint64_t*>(sm + TL::kBar), 1);
   __syncthreads();
+  pdl_wait();
   uint32_t phase = 0;
   for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
     const int2 item = b.tiles[t];
@@ -381,14 +385,30 @@ __global__ void __launch_bounds__(Tile1D<T, FluxM<FLUX>::m>::NT) stage1d_batched
 // ---------------------------------------------------------------------------------------
 // Host-side launchers, instantiated per policy
 // ---------------------------------------------------------------------------------------
+
+// Launch with programmatic stream serialization: the kernel may start while its predecessor in
+// the stream finishes, and waits for it with griddepcontrol.wait before touching its outputs.
+template <class K, class A>
+cudaError_t launch_pdl(K kern, dim3 grid, dim3 block, size_t smem, cudaStream_t st, const A& arg) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, arg);
+}
 template <class MATH, int FLUX, int STAGE, int T>
 cudaError_t launch_stage1d_t(const Stage1DArgs& a, cudaStream_t st) {
   using TL = Tile1D<T, FluxM<FLUX>::m>;
   static_assert(TL::bytes <= 48 * 1024, "tile exceeds the default dynamic shared memory limit");
   auto kern = stage1d_kernel<MATH, FLUX, STAGE, T>;
   const unsigned grid = (unsigned)((a.n + T - 1) / T);
-  kern<<<grid, TL::NT, TL::bytes, st>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(kern, dim3(grid), dim3(TL::NT), TL::bytes, st, a);
 }
 
 template <class MATH, int FLUX, int T>
@@ -438,8 +458,7 @@ cudaError_t launch_alpha1d_policy(int flux, const double* u, long long n, long l
 template <class MATH, int FLUX, int STAGE, int T>
 cudaError_t launch_stage1d_batched_t(const BatchArgs& b, int grid, cudaStream_t st) {
   using TL = Tile1D<T, FluxM<FLUX>::m>;
-  stage1d_batched_kernel<MATH, FLUX, STAGE, T><<<grid, TL::NT, TL::bytes, st>>>(b);
-  return cudaGetLastError();
+  return launch_pdl(stage1d_batched_kernel<MATH, FLUX, STAGE, T>, dim3(grid), dim3(TL::NT), TL::bytes, st, b);
 }
 
 template <class MATH, int FLUX, int T>

@@ -96,6 +96,8 @@ __global__ void __launch_bounds__(Tile2D<TX, TY>::NT) stage2d_kernel(const Stage
   double* s_Lx = sm + TL::kLx;
   double* s_red = sm + TL::kRed;
 
+  pdl_launch_dependents();
+  pdl_wait();
   const int tid = threadIdx.x;
   Ctl* ctl = a.ctl;
   const long long nx = a.nx, ny = a.ny;
@@ -363,8 +365,7 @@ cudaError_t launch_stage2d_t(const Stage2DArgs& a, cudaStream_t st) {
   using TL = Tile2D<TX, TY>;
   auto kern = stage2d_kernel<MATH, STAGE, TX, TY>;  // prepare_stage2d_policy() raised its shared-memory limit
   dim3 grid((unsigned)((a.nx + TX - 1) / TX), (unsigned)((a.ny + TY - 1) / TY));
-  kern<<<grid, TL::NT, TL::bytes, st>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(kern, grid, dim3(TL::NT), TL::bytes, st, a);
 }
 
 template <class MATH>
