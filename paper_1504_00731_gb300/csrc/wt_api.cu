@@ -698,6 +698,25 @@ int adjoint_layout(const wt_problem* prob, const wt_grid* grid, int nprob, int64
   return WT_OK;
 }
 
+// Reads the control block back, reports a device-detected failure, copies u^n to the caller.
+int finish_step_1d(Ctl* ctl, double* Un, const Layout1D& lay, double* u, bool u_dev, double* st_in, int m,
+                          long long n, double* t_reached, int64_t* steps, cudaStream_t st) {
+  Ctl hc;
+  WT_CUDA(cudaMemcpyAsync(&hc, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+  WT_CUDA(cudaStreamSynchronize(st));
+  if (hc.status != 0) return fail(hc.status, "device reported status %d after %lld steps", hc.status, hc.steps);
+  if (u_dev) {
+    WT_CUDA(launch_unpack1d(Un, lay.pitch, u, n, n, m, st));
+  } else {
+    WT_CUDA(launch_unpack1d(Un, lay.pitch, st_in, n, n, m, st));
+    WT_CUDA(cudaMemcpyAsync(u, st_in, sizeof(double) * m * n, cudaMemcpyDeviceToHost, st));
+  }
+  WT_CUDA(cudaStreamSynchronize(st));
+  if (t_reached) *t_reached = hc.t;
+  if (steps) *steps = hc.steps;
+  return WT_OK;
+}
+
 }  // namespace
 
 int wt::set_last_error(int code, const char* msg) { return fail(code, "%s", msg); }
@@ -818,6 +837,60 @@ int weno_theta_step(const wt_problem* prob, const wt_grid* grid, double* u, doub
   a[2].uin = U2;
   a[2].un = Un;
   a[2].uout = Un;
+  Ctl hc;
+  const bool bounded_time = std::isfinite(t_final);
+  // Launch strategy, by how the grid's tiles fit on the device:
+  //   at most one tile per SM: the step-blocked persistent kernel (one cooperative launch per
+  //     chunk of steps, halo exchange once per RK step);
+  //   all tiles co-resident: the persistent kernel with a halo exchange per stage;
+  //   otherwise: CUDA graphs of the three stage kernels of an RK step.
+  const bool strict = prob->mode == WT_MODE_STRICT;
+  const int tsb = stepblock1d_tile(prob->flux);
+  const long long nsb = (n + tsb - 1) / tsb;
+  int nsm = 0;
+  WT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const long long ntiles = (n + tile - 1) / tile;
+  int kind = 0, pgrid = 0;
+  if (max_steps > 0) {
+    const int cap_sb = strict ? stepblock1d_capacity_strict(prob->flux) : stepblock1d_capacity_fast(prob->flux);
+    if (nsb <= nsm && nsb <= cap_sb) {
+      kind = 2;
+      pgrid = (int)nsb;
+    } else {
+      const int cap = strict ? persist1d_capacity_strict(prob->flux, tile) : persist1d_capacity_fast(prob->flux, tile);
+      if (cap > 0 && ntiles <= cap) {
+        kind = 1;
+        pgrid = (int)ntiles;
+      }
+    }
+  }
+  if (kind != 0) {
+    PersistArgs pa;
+    for (int s = 0; s < 3; ++s) pa.a[s] = a[s];
+    constexpr int64_t kChunk = 4096;
+    int64_t done = 0;
+    while (done < max_steps) {
+      int64_t k = max_steps - done;
+      if (k > kChunk) k = kChunk;
+      pa.n_steps = k;
+      WT_CUDA(cudaMemsetAsync(&ctl->gbar, 0, sizeof(unsigned long long) + 4 * sizeof(unsigned int), st));
+      if (kind == 2) {
+        WT_CUDA(strict ? launch_stepblock1d_strict(prob->flux, pa, pgrid, st)
+                       : launch_stepblock1d_fast(prob->flux, pa, pgrid, st));
+      } else {
+        WT_CUDA(strict ? launch_persist1d_strict(prob->flux, tile, pa, pgrid, st)
+                       : launch_persist1d_fast(prob->flux, tile, pa, pgrid, st));
+      }
+      done += k;
+      if (done < max_steps) {
+        WT_CUDA(cudaMemcpyAsync(&hc, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+        WT_CUDA(cudaStreamSynchronize(st));
+        if (hc.status != 0 || !(hc.t < hc.t_final)) break;
+      }
+    }
+    return finish_step_1d(ctl, Un, lay, u, u_dev, st_in, m, n, t_reached, steps, st);
+  }
+
   // RK steps replay from graphs of kGraphSteps steps (programmatic edges between their stage
   // launches) plus a one-step graph for the remainder
   constexpr int kGraphSteps = 8;
@@ -825,9 +898,7 @@ int weno_theta_step(const wt_problem* prob, const wt_grid* grid, double* u, doub
   if (max_steps > 0 && (rc = get_step_graph(prob, dev, tile, 1, a, &exec1)) != WT_OK) return rc;
   if (max_steps >= kGraphSteps && (rc = get_step_graph(prob, dev, tile, kGraphSteps, a, &execK)) != WT_OK) return rc;
 
-  Ctl hc;
   int64_t launched = 0;
-  const bool bounded_time = std::isfinite(t_final);
   const int64_t chunk = bounded_time ? 64 : max_steps;
   while (launched < max_steps) {
     int64_t k = max_steps - launched;
@@ -842,19 +913,7 @@ int weno_theta_step(const wt_problem* prob, const wt_grid* grid, double* u, doub
       if (hc.status != 0 || !(hc.t < hc.t_final)) break;
     }
   }
-  WT_CUDA(cudaMemcpyAsync(&hc, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
-  WT_CUDA(cudaStreamSynchronize(st));
-  if (hc.status != 0) return fail(hc.status, "device reported status %d after %lld steps", hc.status, hc.steps);
-  if (u_dev) {
-    WT_CUDA(launch_unpack1d(Un, lay.pitch, u, n, n, m, st));
-  } else {
-    WT_CUDA(launch_unpack1d(Un, lay.pitch, st_in, n, n, m, st));
-    WT_CUDA(cudaMemcpyAsync(u, st_in, sizeof(double) * m * n, cudaMemcpyDeviceToHost, st));
-  }
-  WT_CUDA(cudaStreamSynchronize(st));
-  if (t_reached) *t_reached = hc.t;
-  if (steps) *steps = hc.steps;
-  return WT_OK;
+  return finish_step_1d(ctl, Un, lay, u, u_dev, st_in, m, n, t_reached, steps, st);
 }
 
 int weno_theta_step_batched(const wt_problem* prob, const wt_segment* segs, int32_t nprob, double* u_packed,

@@ -28,6 +28,10 @@ struct Ctl {
   int status;                     // first device-detected failure (wt_status), 0 if none
   int active;                     // 1 while the current step is being taken
   int pad[2];
+  // persistent kernel: grid-barrier arrivals of the launch, and per-step stop votes (ring of 3)
+  unsigned long long gbar;
+  unsigned int vote[3];
+  int pad2;
 };
 
 __device__ __forceinline__ void flag_error(Ctl* ctl, int code) {
@@ -89,37 +93,95 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 }
 
 // ---------------------------------------------------------------------------------------
-// Block-wide maxima of non-negative doubles (bit patterns order like the values)
+// Block-wide maxima of wave speeds, on bit patterns.  Speeds are non-negative, and
+// non-negative doubles order like their bit patterns, so the maxima run on the integer
+// pipe instead of the narrow FP64 one.  A NaN speed (the sound speed of a finite state
+// whose pressure went negative) maps to key 0 and so drops out of the maximum.
 // ---------------------------------------------------------------------------------------
 
-__device__ __forceinline__ double warp_max(double v) {
+__device__ __forceinline__ unsigned long long speed_key(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  return b > 0x7FF0000000000000ull ? 0ull : b;
+}
+__device__ __forceinline__ void key_max(unsigned long long& acc, double x) {
+  const unsigned long long k = speed_key(x);
+  acc = (acc < k) ? k : acc;
+}
+
+__device__ __forceinline__ unsigned long long warp_max_key(unsigned long long v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    double w = __shfl_xor_sync(0xffffffffu, v, o);
+    const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
     v = (v < w) ? w : v;
   }
   return v;
 }
 
-// Reduces K values per thread to the block maximum and folds it into dst[k] with one
+// Reduces K keys per thread to the block maximum and folds it into dst[k] with one
 // atomicMax per block.  scratch: >= K * 32 doubles of shared memory.
 template <int K>
-__device__ __forceinline__ void block_max_atomic(double (&v)[K], double* scratch, unsigned long long* dst) {
+__device__ __forceinline__ void block_max_atomic(unsigned long long (&v)[K], double* scratch_d,
+                                                 unsigned long long* dst) {
+  unsigned long long* scratch = reinterpret_cast<unsigned long long*>(scratch_d);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    double w = warp_max(v[k]);
+    const unsigned long long w = warp_max_key(v[k]);
     if (lane == 0) scratch[k * 32 + warp] = w;
   }
   __syncthreads();
   if (threadIdx.x < K) {
-    double m = 0.0;
+    unsigned long long m = 0ull;
     for (int w = 0; w < nw; ++w) {
-      double x = scratch[threadIdx.x * 32 + w];
+      const unsigned long long x = scratch[threadIdx.x * 32 + w];
       m = (m < x) ? x : m;
     }
-    if (m > 0.0 || m == 0.0) atomicMax(&dst[threadIdx.x], (unsigned long long)__double_as_longlong(m));
+    atomicMax(&dst[threadIdx.x], m);
   }
+}
+
+// ---------------------------------------------------------------------------------------
+// Grid-wide barrier of a cooperative (co-resident) grid.  ctr counts arrivals from 0 at the
+// launch; the k-th barrier of the launch (k = 1, 2, ...) waits for k * gridDim.x of them.
+// The stores of the block before the barrier are visible to every block after it (fence +
+// release by arrival, acquire by the waiting thread, then a CTA barrier).  Data written
+// during the launch by other blocks must be read around L1 (ld.global.cg).  The wait is
+// bounded: false (for every thread of the block) once about 2^31 clocks have passed.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// arrival: every thread's earlier stores are ordered before it (CTA barrier, then a gpu fence)
+__device__ __forceinline__ void grid_arrive(unsigned long long* ctr) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(ctr, 1ull);
+  }
+}
+
+// wait for `target` arrivals; false for every thread of the block on timeout
+__device__ __forceinline__ bool grid_wait(const unsigned long long* ctr, unsigned long long target) {
+  int bad = 0;
+  if (threadIdx.x == 0) {
+    const long long start = clock64();
+    while (ld_acquire_u64(ctr) < target) {
+      if (clock64() - start > (1LL << 31)) {
+        bad = 1;
+        break;
+      }
+    }
+    __threadfence();
+  }
+  return __syncthreads_or(bad) == 0;
+}
+
+__device__ __forceinline__ bool grid_barrier(unsigned long long* ctr, unsigned long long target) {
+  grid_arrive(ctr);
+  return grid_wait(ctr, target);
 }
 
 __device__ __forceinline__ double bits_to_double(unsigned long long b) { return __longlong_as_double((long long)b); }

@@ -31,10 +31,17 @@ struct Tile1D {
   static constexpr int kSr = kH + W;
   static constexpr int kL = kSr + W;
   static constexpr int kRs = kL + 9 * NI;
-  static constexpr int kFs = kRs + 3 * NI;
-  static constexpr int kHf = kFs + M * NI;
+  static constexpr int kFs = kRs + 3 * NI;       // F+ [M][NI], then F- [M][NI]
+  static constexpr int kHf = kFs + 2 * M * NI;
   static constexpr int kRed = kHf + M * NI;
-  static constexpr int kTotal = kRed + 4 * 32;
+  static constexpr int kQn = kRed + 4 * 32;      // queue length (int)
+  static constexpr int kQ = kQn + 2;             // queue records [9][QCAP]
+  // queue of reconstructions whose weights are still to be evaluated: one slot per thread,
+  // fewer if the tile would pass 48 KB (the rest evaluate their weights in place)
+  static constexpr int kQFit = ((48 * 1024 / 8 - kQ) * 2) / 19;
+  static constexpr int QCAP = (kQFit < NT ? kQFit : NT) & ~1;
+  static constexpr int kQi = kQ + 9 * QCAP;      // record destinations (int)
+  static constexpr int kTotal = kQi + QCAP / 2;
   static constexpr size_t bytes = sizeof(double) * kTotal;
 };
 
@@ -55,9 +62,9 @@ __global__ void __launch_bounds__(256) alpha1d_kernel(const double* __restrict__
                                                       double gamma, double adv, Ctl* ctl, int slot) {
   constexpr int M = FluxM<FLUX>::m;
   __shared__ double red[4 * 32];
-  double v[M];
+  unsigned long long v[M];
 #pragma unroll
-  for (int s = 0; s < M; ++s) v[s] = 0.0;
+  for (int s = 0; s < M; ++s) v[s] = 0ull;
   for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x) {
     if (FLUX == WT_FLUX_EULER1D) {
       double U[3] = {u[j + G], u[pitch + j + G], u[2 * pitch + j + G]};
@@ -65,12 +72,12 @@ __global__ void __launch_bounds__(256) alpha1d_kernel(const double* __restrict__
       MATH::euler_speeds(U, gamma, lam);
       if (!finite3(U)) flag_error(ctl, WT_ERR_NONPHYSICAL);
 #pragma unroll
-      for (int s = 0; s < M; ++s) v[s] = (v[s] < lam[s]) ? lam[s] : v[s];
+      for (int s = 0; s < M; ++s) key_max(v[s], lam[s]);
     } else {
       double x = u[j + G];
       double lam = (FLUX == WT_FLUX_ADVECTION) ? fabs(adv) : fabs(x);
       if (!isfinite(x)) flag_error(ctl, WT_ERR_NONPHYSICAL);
-      v[0] = (v[0] < lam) ? lam : v[0];
+      key_max(v[0], lam);
     }
   }
   block_max_atomic<M>(v, red, ctl->amax[slot]);
@@ -86,9 +93,9 @@ __global__ void __launch_bounds__(256) alpha1d_batched_kernel(const double* __re
   const BatchSeg sg = segs[blockIdx.y];
   Ctl* c = ctl + blockIdx.y;
   const double* up = u + sg.poff;
-  double v[M];
+  unsigned long long v[M];
 #pragma unroll
-  for (int s = 0; s < M; ++s) v[s] = 0.0;
+  for (int s = 0; s < M; ++s) v[s] = 0ull;
   for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < sg.n;
        j += (long long)gridDim.x * blockDim.x) {
     if (FLUX == WT_FLUX_EULER1D) {
@@ -97,12 +104,12 @@ __global__ void __launch_bounds__(256) alpha1d_batched_kernel(const double* __re
       MATH::euler_speeds(U, gamma, lam);
       if (!finite3(U)) flag_error(c, WT_ERR_NONPHYSICAL);
 #pragma unroll
-      for (int s = 0; s < M; ++s) v[s] = (v[s] < lam[s]) ? lam[s] : v[s];
+      for (int s = 0; s < M; ++s) key_max(v[s], lam[s]);
     } else {
       double x = up[j + G];
       double lam = (FLUX == WT_FLUX_ADVECTION) ? fabs(adv) : fabs(x);
       if (!isfinite(x)) flag_error(c, WT_ERR_NONPHYSICAL);
-      v[0] = (v[0] < lam) ? lam : v[0];
+      key_max(v[0], lam);
     }
   }
   block_max_atomic<M>(v, red, c->amax[0]);
@@ -117,13 +124,37 @@ __global__ void __launch_bounds__(256) alpha1d_batched_kernel(const double* __re
 //   D  per interface: back-projection to the interface flux h_{j+1/2}
 //   E  per cell: flux difference, RK combine, ghost images, wave speeds of the new state
 // ---------------------------------------------------------------------------------------
-template <class MATH, int FLUX, int STAGE, int T>
-__device__ __forceinline__ bool stage1d_tile(const Stage1DArgs& a, const long long j0, const bool first_tile, double* sm,
-                                             uint32_t& phase) {
+// How a tile's stage sits in its kernel:
+//   kStage        one launch per stage; the window is bulk-copied in, outputs go to global memory
+//   kResident     persistent kernel: the stage output of the tile's cells also stays in shared
+//                 memory (s_uin, and s_un after the last stage); halos are exchanged per stage
+//   kStepBlocked  persistent kernel whose tiles carry 9 redundant halo cells per side, so the
+//                 three stages of an RK step need no halo exchange: the computed range shrinks
+//                 by 3 cells per side per stage, only the tile's own cells contribute to the
+//                 alphas, and only the last stage writes global memory
+enum { kStage = 0, kResident = 1, kStepBlocked = 2 };
+
+// Alphas of the stage still to be produced by the other CTAs: wait for `target` arrivals on
+// ctl->gbar (target 0: the alphas are given), then read ctl->amax[slot]; the CTA with
+// clear >= 0 then zeroes that slot of the ring.
+struct AlphaWait {
+  unsigned long long target;
+  int slot, clear;
+};
+
+// Phases B-E of one stage over the cells [js, js + Ts) whose window [js - 3, js + Ts + 3) is
+// in shared memory at s_uin[off...] (s_un for stages 2 and 3), with the stage's dt.  Ends
+// with the block's wave-speed maxima (cells of [own_lo, own_hi)) folded into the next alpha
+// slot.  Returns false if a wait for the alphas timed out.
+template <class MATH, int FLUX, int STAGE, int T, int MODE>
+__device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long long js, const int Ts, const int off,
+                                                const long long own_lo, const long long own_hi,
+                                                double (&alpha)[FluxM<FLUX>::m], const double dt, double* sm,
+                                                const AlphaWait aw) {
   constexpr int M = FluxM<FLUX>::m;
   using TL = Tile1D<T, M>;
   constexpr int W = TL::W, NI = TL::NI, NT = TL::NT;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + TL::kBar);
+  static_assert(NT >= M * NI, "one (interface, field) item per thread");
   double* s_uin = sm + TL::kUin;
   double* s_un = sm + TL::kUn;
   double* s_f = sm + TL::kF;
@@ -135,69 +166,16 @@ __device__ __forceinline__ bool stage1d_tile(const Stage1DArgs& a, const long lo
   double* s_F = sm + TL::kFs;
   double* s_h = sm + TL::kHf;
   double* s_red = sm + TL::kRed;
-
   const int tid = threadIdx.x;
   Ctl* ctl = a.ctl;
   const long long n = a.n;
-  if (j0 >= n) return true;
-  const int Tc = (int)((n - j0 < T) ? (n - j0) : T);
+  const int Tc = Ts;
   const int ni = Tc + 1;
-  // ---- step control: is this step active, and its dt
-  double dt = 0.0;
-  if (STAGE != STAGE_RHS) {
-    if (STAGE == STAGE_RK1) {
-      const bool act = (ctl->status == 0) && (ctl->t < ctl->t_final);
-      if (!act) {
-        if (first_tile && tid == 0) ctl->active = 0;
-        return true;
-      }
-    } else if (ctl->active == 0) {
-      return true;
-    }
-    if (first_tile && tid < 8) ctl->amax[(STAGE + 2) % 3][tid] = 0ull;
-  }
-  const int slot_in = (STAGE == STAGE_RHS) ? 0 : STAGE;
-  double alpha[M];
-#pragma unroll
-  for (int s = 0; s < M; ++s) alpha[s] = bits_to_double(ctl->amax[slot_in][s]);
-  if (STAGE == STAGE_RK1) {
-    const double smax = (FLUX == WT_FLUX_EULER1D) ? ((alpha[0] < alpha[M - 1]) ? alpha[M - 1] : alpha[0]) : alpha[0];
-    dt = ctl->dt_fixed > 0.0 ? ctl->dt_fixed : MATH::cfl_dt(ctl->cfl, a.dx, smax);
-    const double rem = ctl->t_final - ctl->t;
-    if (rem < dt) dt = rem;
-    if (first_tile && tid == 0) {
-      ctl->dt = dt;
-      ctl->active = 1;
-    }
-  } else if (STAGE != STAGE_RHS) {
-    dt = ctl->dt;
-  }
-
-  // ---- A: stage the window [j0 - 3, j0 + Tc + 3) of every plane (16-byte aligned start)
-  const long long s0 = j0 & ~1LL;
-  const int off = (int)(j0 - s0);
   const int cells = Tc + 2 * G;
-  const int len = (off + cells + 1) & ~1;
   constexpr bool kNeedUn = (STAGE == STAGE_RK2 || STAGE == STAGE_RK3);
-  if (tid == 0) {
-    const uint32_t bytes = (uint32_t)len * 8u;
-    mbar_arrive_expect_tx(bar, bytes * (kNeedUn ? 2 * M : M));
-#pragma unroll
-    for (int c = 0; c < M; ++c) bulk_g2s(s_uin + c * W, a.uin + c * a.pitch + s0, bytes, bar);
-    if (kNeedUn) {
-#pragma unroll
-      for (int c = 0; c < M; ++c) bulk_g2s(s_un + c * W, a.un + c * a.pitch + s0, bytes, bar);
-    }
-  }
-  const bool ok = mbar_wait_bounded(bar, phase);
-  if (__syncthreads_or(ok ? 0 : 1)) {
-    if (tid == 0) flag_error(ctl, WT_ERR_TIMEOUT);
-    mbar_wait_bounded(bar, phase);
-    return false;
-  }
-  phase ^= 1u;
 
   // ---- B: per-cell quantities
+  if (tid == 0) *reinterpret_cast<int*>(sm + TL::kQn) = 0;
   for (int k = tid; k < cells; k += NT) {
     if (FLUX == WT_FLUX_EULER1D) {
       double U[3] = {s_uin[off + k], s_uin[W + off + k], s_uin[2 * W + off + k]};
@@ -231,40 +209,100 @@ __device__ __forceinline__ bool stage1d_tile(const Stage1DArgs& a, const long lo
     __syncthreads();
   }
 
-  // ---- C1: per (interface, field) reconstruction on both sides
-  for (int item = tid; item < M * ni; item += NT) {
-    const int s = item / ni;
-    const int i = item - s * ni;
-    double vp[6], vm[6];
+  // ---- C1: per (interface, field) reconstruction on both sides.  The projections onto the
+  // characteristic field split into the alpha-free products (l.f, l.u), taken first, and the
+  // Lax-Friedrichs combination.  A side whose stencil is not restricted (Eq. (be_res)) queues
+  // its weight evaluation, which a second pass spreads over full warps instead of diverging
+  // inside the first.
+  int* s_qn = reinterpret_cast<int*>(sm + TL::kQn);
+  double* s_q = sm + TL::kQ;
+  int* s_qi = reinterpret_cast<int*>(sm + TL::kQi);
+  constexpr int QCAP = TL::QCAP;
+  const bool has_item = tid < M * ni;
+  const int s = has_item ? tid / ni : 0;
+  const int i = tid - s * ni;
+  double pa[6], pb[6];
+  if (has_item) {
     if (FLUX == WT_FLUX_EULER1D) {
       double l[3] = {s_L[(3 * s) * NI + i], s_L[(3 * s + 1) * NI + i], s_L[(3 * s + 2) * NI + i]};
-      double al = (s == 0) ? alpha[0] : ((s == 1) ? alpha[1] : alpha[M - 1]);
 #pragma unroll
       for (int kk = 0; kk < 6; ++kk) {
         const int k = i + kk;
         double f[3] = {s_f[k], s_f[W + k], s_f[2 * W + k]};
         double U[3] = {s_uin[off + k], s_uin[W + off + k], s_uin[2 * W + off + k]};
-        MATH::project3(l, f, U, al, vp[kk], vm[kk]);
+        MATH::project3_ab(l, f, U, pa[kk], pb[kk]);
       }
     } else {
 #pragma unroll
-      for (int kk = 0; kk < 6; ++kk) MATH::project1(s_f[i + kk], s_uin[off + i + kk], alpha[0], vp[kk], vm[kk]);
+      for (int kk = 0; kk < 6; ++kk) MATH::project1_ab(s_f[i + kk], s_uin[off + i + kk], pa[kk], pb[kk]);
     }
+  }
+  if (MODE == kStepBlocked && aw.target != 0ull) {
+    if (!grid_wait(&ctl->gbar, aw.target)) return false;
+#pragma unroll
+    for (int f = 0; f < M; ++f) alpha[f] = bits_to_double(__ldcg(&ctl->amax[aw.slot][f]));
+    if (aw.clear >= 0 && tid < 8) ctl->amax[aw.clear][tid] = 0ull;
+  }
+  if (has_item) {
+    const double al = (s == 0) ? alpha[0] : ((s == 1) ? alpha[1] : alpha[M - 1]);
+    double vp[6], vm[6];
+#pragma unroll
+    for (int kk = 0; kk < 6; ++kk) MATH::project_v(pa[kk], pb[kk], al, vp[kk], vm[kk]);
     double qm[6];
 #pragma unroll
     for (int kk = 0; kk < 6; ++kk) qm[kk] = vm[5 - kk];
-    const double Fp = MATH::weno(vp, a.eps, a.alpha_R);
-    const double Fm = MATH::weno(qm, a.eps, a.alpha_R);
-    s_F[s * NI + i] = Fp + Fm;
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const double* q = side ? qm : vp;
+      const int dst = side * (M * NI) + s * NI + i;
+      if constexpr (MATH::kSplitWeno) {
+        typename MATH::WenoPart w;
+        double out;
+        if (MATH::weno_begin(q, a.eps, a.alpha_R, out, w)) {
+          s_F[dst] = out;
+        } else {
+          const int slot = atomicAdd(s_qn, 1);
+          if (slot < QCAP) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) s_q[k * QCAP + slot] = w.e[k];
+            s_q[4 * QCAP + slot] = w.tau;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) s_q[(5 + k) * QCAP + slot] = w.fh[k];
+            s_qi[slot] = dst | (w.theta1 ? (1 << 30) : 0);
+          } else {
+            s_F[dst] = MATH::weno_finish(w);
+          }
+        }
+      } else {
+        s_F[dst] = MATH::weno(q, a.eps, a.alpha_R);
+      }
+    }
   }
   __syncthreads();
+  if constexpr (MATH::kSplitWeno) {
+    const int nq = min(*s_qn, QCAP);  // the same for every thread of the block
+    if (nq > 0) {
+      for (int t = tid; t < nq; t += NT) {
+        typename MATH::WenoPart w;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) w.e[k] = s_q[k * QCAP + t];
+        w.tau = s_q[4 * QCAP + t];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) w.fh[k] = s_q[(5 + k) * QCAP + t];
+        const int d = s_qi[t];
+        w.theta1 = (d >> 30) & 1;
+        s_F[d & ((1 << 30) - 1)] = MATH::weno_finish(w);
+      }
+      __syncthreads();
+    }
+  }
 
   // ---- D: interface fluxes h_{j+1/2} = R (F+ + F-)
   const double* hsrc = s_F;
   if (FLUX == WT_FLUX_EULER1D) {
     for (int i = tid; i < ni; i += NT) {
       double rs[3] = {s_rs[i], s_rs[NI + i], s_rs[2 * NI + i]};
-      double F[3] = {s_F[i], s_F[NI + i], s_F[2 * NI + i]};
+      double F[3] = {s_F[i] + s_F[3 * NI + i], s_F[NI + i] + s_F[4 * NI + i], s_F[2 * NI + i] + s_F[5 * NI + i]};
       double h[3];
       MATH::backproject(rs, F, h);
 #pragma unroll
@@ -275,15 +313,19 @@ __device__ __forceinline__ bool stage1d_tile(const Stage1DArgs& a, const long lo
   }
 
   // ---- E: flux difference, RK combine, ghost images, wave speeds
-  double vmax[M];
+  unsigned long long vmax[M];
 #pragma unroll
-  for (int s = 0; s < M; ++s) vmax[s] = 0.0;
+  for (int f = 0; f < M; ++f) vmax[f] = 0ull;
   for (int t = tid; t < Tc; t += NT) {
-    const long long j = j0 + t;
+    const long long j = js + t;
+    const bool own = (MODE != kStepBlocked) || (j >= own_lo && j < own_hi);
     double uo[M];
 #pragma unroll
     for (int c = 0; c < M; ++c) {
-      const double L = MATH::flux_diff(hsrc[c * NI + t + 1], hsrc[c * NI + t], a.dx, a.inv_dx);
+      // scalar fluxes: h = F+ + F- directly from the reconstruction
+      const double hp = (FLUX == WT_FLUX_EULER1D) ? hsrc[c * NI + t + 1] : hsrc[t + 1] + hsrc[NI + t + 1];
+      const double hm = (FLUX == WT_FLUX_EULER1D) ? hsrc[c * NI + t] : hsrc[t] + hsrc[NI + t];
+      const double L = MATH::flux_diff(hp, hm, a.dx, a.inv_dx);
       if (STAGE == STAGE_RHS) {
         a.Lout[c * a.lout_stride + j] = L;
       } else {
@@ -293,38 +335,124 @@ __device__ __forceinline__ bool stage1d_tile(const Stage1DArgs& a, const long lo
       }
     }
     if (STAGE != STAGE_RHS) {
-#pragma unroll
-      for (int c = 0; c < M; ++c) a.uout[c * a.pitch + j + G] = uo[c];
-      // ghost images of this cell in the output
-      if (j < G || j >= n - G) {
+      if (MODE != kStage) {
 #pragma unroll
         for (int c = 0; c < M; ++c) {
-          double* o = a.uout + c * a.pitch;
-          const double v = uo[c];
-          const double vr = (c == 1) ? -v : v;
-          if (a.bc_hi == WT_BC_PERIODIC && j < G) o[n + j + G] = v;
-          if (a.bc_lo == WT_BC_PERIODIC && j >= n - G) o[j - n + G] = v;
-          if (a.bc_lo == WT_BC_OUTFLOW && j == 0) o[0] = o[1] = o[2] = v;
-          if (a.bc_hi == WT_BC_OUTFLOW && j == n - 1) o[n + 3] = o[n + 4] = o[n + 5] = v;
-          if (a.bc_lo == WT_BC_REFLECTIVE && j < G) o[2 - j] = vr;
-          if (a.bc_hi == WT_BC_REFLECTIVE && j >= n - G) o[2 * n + 2 - j] = vr;
+          s_uin[c * W + off + t + G] = uo[c];
+          if (STAGE == STAGE_RK3) s_un[c * W + off + t + G] = uo[c];
         }
       }
-      if (FLUX == WT_FLUX_EULER1D) {
-        double lam[3];
-        MATH::euler_speeds(uo, a.gamma, lam);
-        if (!finite3(uo)) flag_error(ctl, WT_ERR_NONPHYSICAL);
+      if (own && (MODE != kStepBlocked || STAGE == STAGE_RK3)) {
 #pragma unroll
-        for (int s = 0; s < M; ++s) vmax[s] = (vmax[s] < lam[s]) ? lam[s] : vmax[s];
-      } else {
-        const double lam = (FLUX == WT_FLUX_ADVECTION) ? fabs(a.adv_speed) : fabs(uo[0]);
-        if (!isfinite(uo[0])) flag_error(ctl, WT_ERR_NONPHYSICAL);
-        vmax[0] = (vmax[0] < lam) ? lam : vmax[0];
+        for (int c = 0; c < M; ++c) a.uout[c * a.pitch + j + G] = uo[c];
+        // ghost images of this cell in the output
+        if (j < G || j >= n - G) {
+#pragma unroll
+          for (int c = 0; c < M; ++c) {
+            double* o = a.uout + c * a.pitch;
+            const double v = uo[c];
+            const double vr = (c == 1) ? -v : v;
+            if (a.bc_hi == WT_BC_PERIODIC && j < G) o[n + j + G] = v;
+            if (a.bc_lo == WT_BC_PERIODIC && j >= n - G) o[j - n + G] = v;
+            if (a.bc_lo == WT_BC_OUTFLOW && j == 0) o[0] = o[1] = o[2] = v;
+            if (a.bc_hi == WT_BC_OUTFLOW && j == n - 1) o[n + 3] = o[n + 4] = o[n + 5] = v;
+            if (a.bc_lo == WT_BC_REFLECTIVE && j < G) o[2 - j] = vr;
+            if (a.bc_hi == WT_BC_REFLECTIVE && j >= n - G) o[2 * n + 2 - j] = vr;
+          }
+        }
+      }
+      if (own) {
+        if (FLUX == WT_FLUX_EULER1D) {
+          double lam[3];
+          MATH::euler_speeds(uo, a.gamma, lam);
+          if (!finite3(uo)) flag_error(ctl, WT_ERR_NONPHYSICAL);
+#pragma unroll
+          for (int f = 0; f < M; ++f) key_max(vmax[f], lam[f]);
+        } else {
+          const double lam = (FLUX == WT_FLUX_ADVECTION) ? fabs(a.adv_speed) : fabs(uo[0]);
+          if (!isfinite(uo[0])) flag_error(ctl, WT_ERR_NONPHYSICAL);
+          key_max(vmax[0], lam);
+        }
       }
     }
   }
+  if (STAGE != STAGE_RHS) block_max_atomic<M>(vmax, s_red, ctl->amax[(STAGE + 1) % 3]);
+  return true;
+}
+
+template <class MATH, int FLUX, int STAGE, int T>
+__device__ __forceinline__ bool stage1d_tile(const Stage1DArgs& a, const long long j0, const bool first_tile, double* sm,
+                                             uint32_t& phase) {
+  constexpr int M = FluxM<FLUX>::m;
+  using TL = Tile1D<T, M>;
+  constexpr int W = TL::W;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + TL::kBar);
+  double* s_uin = sm + TL::kUin;
+  double* s_un = sm + TL::kUn;
+  int* s_run = reinterpret_cast<int*>(sm + TL::kQn) + 1;
+  const int tid = threadIdx.x;
+  Ctl* ctl = a.ctl;
+  const long long n = a.n;
+  if (j0 >= n) return true;
+  const int Tc = (int)((n - j0 < T) ? (n - j0) : T);
+
+  // ---- A: stage the window [j0 - 3, j0 + Tc + 3) of every plane (16-byte aligned start).
+  // The copies are issued first and overlap the reads of the control block below.
+  const long long s0 = j0 & ~1LL;
+  const int off = (int)(j0 - s0);
+  const int cells = Tc + 2 * G;
+  const int len = (off + cells + 1) & ~1;
+  constexpr bool kNeedUn = (STAGE == STAGE_RK2 || STAGE == STAGE_RK3);
+  if (tid == 0) {
+    const uint32_t bytes = (uint32_t)len * 8u;
+    mbar_arrive_expect_tx(bar, bytes * (kNeedUn ? 2 * M : M));
+#pragma unroll
+    for (int c = 0; c < M; ++c) bulk_g2s(s_uin + c * W, a.uin + c * a.pitch + s0, bytes, bar);
+    if (kNeedUn) {
+#pragma unroll
+      for (int c = 0; c < M; ++c) bulk_g2s(s_un + c * W, a.un + c * a.pitch + s0, bytes, bar);
+    }
+  }
+
+  // ---- step control: is this step active (decided by thread 0 for the whole block), its dt
+  if (tid == 0) {
+    int run = 1;
+    if (STAGE == STAGE_RK1) run = (ctl->status == 0) && (ctl->t < ctl->t_final);
+    if (STAGE == STAGE_RK2 || STAGE == STAGE_RK3) run = ctl->active != 0;
+    if (STAGE == STAGE_RK1 && !run && first_tile) ctl->active = 0;
+    *s_run = run;
+  }
+  double dt = 0.0;
+  double alpha[M];
+  const int slot_in = (STAGE == STAGE_RHS) ? 0 : STAGE;
+#pragma unroll
+  for (int s = 0; s < M; ++s) alpha[s] = bits_to_double(ctl->amax[slot_in][s]);
+  if (STAGE == STAGE_RK1) {
+    const double smax = (FLUX == WT_FLUX_EULER1D) ? ((alpha[0] < alpha[M - 1]) ? alpha[M - 1] : alpha[0]) : alpha[0];
+    dt = ctl->dt_fixed > 0.0 ? ctl->dt_fixed : MATH::cfl_dt(ctl->cfl, a.dx, smax);
+    const double rem = ctl->t_final - ctl->t;
+    if (rem < dt) dt = rem;
+  } else if (STAGE != STAGE_RHS) {
+    dt = ctl->dt;
+  }
+
+  // every copy completes before the block moves on (or leaves)
+  const bool ok = mbar_wait_bounded(bar, phase);
+  if (__syncthreads_or(ok ? 0 : 1)) {
+    if (tid == 0) flag_error(ctl, WT_ERR_TIMEOUT);
+    mbar_wait_bounded(bar, phase);
+    return false;
+  }
+  phase ^= 1u;
+  if (!*s_run) return true;
+  if (STAGE != STAGE_RHS && first_tile && tid < 8) ctl->amax[(STAGE + 2) % 3][tid] = 0ull;
+  if (STAGE == STAGE_RK1 && first_tile && tid == 0) {
+    ctl->dt = dt;
+    ctl->active = 1;
+  }
+
+  stage1d_compute<MATH, FLUX, STAGE, T, kStage>(a, j0, Tc, off, j0, j0 + Tc, alpha, dt, sm, AlphaWait{0ull, 0, -1});
   if (STAGE != STAGE_RHS) {
-    block_max_atomic<M>(vmax, s_red, ctl->amax[(STAGE + 1) % 3]);
     if (STAGE == STAGE_RK3 && first_tile && tid == 0) {
       ctl->t = ctl->t + dt;
       ctl->steps = ctl->steps + 1;
@@ -383,6 +511,300 @@ __global__ void __launch_bounds__(Tile1D<T, FluxM<FLUX>::m>::NT) stage1d_batched
 }
 
 // ---------------------------------------------------------------------------------------
+// Persistent RK3 integration of one problem: a cooperative grid with one CTA per tile runs
+// p.n_steps steps (fewer once t_final is reached or a failure was flagged), three stages per
+// step, with a grid barrier after each stage instead of a kernel boundary.  Each CTA keeps
+// its tile resident in shared memory: its own cells of the stage input and of u^n stay
+// there from stage to stage, and only the three halo cells on each side are read back from
+// the neighbours' stage outputs.  Every stage writes its output and ghost images to global
+// memory as in the stage kernels, so the buffers hold the same values on exit.  dt and t
+// are computed by every CTA from the same alphas, so all CTAs take the same decisions; the
+// stop decision of a step is the OR of one vote per CTA (status seen before the step's last
+// barrier), read after that barrier.
+// ---------------------------------------------------------------------------------------
+template <class MATH, int FLUX, int T>
+__device__ __forceinline__ void load_halos(const double* uin, long long pitch, long long j0, int Tc, double* s_uin) {
+  constexpr int M = FluxM<FLUX>::m;
+  constexpr int W = Tile1D<T, M>::W;
+  const int tid = threadIdx.x;
+  if (tid < 2 * G * M) {
+    const int c = tid / (2 * G), h = tid - c * (2 * G);
+    const int k = (h < G) ? h : Tc + h;  // window index: 0..2 and Tc+3..Tc+5
+    s_uin[c * W + k] = __ldcg(uin + c * pitch + j0 + k);
+  }
+  __syncthreads();
+}
+
+template <class MATH, int FLUX, int T>
+__global__ void __launch_bounds__(Tile1D<T, FluxM<FLUX>::m>::NT) persist1d_kernel(const PersistArgs p) {
+  constexpr int M = FluxM<FLUX>::m;
+  using TL = Tile1D<T, M>;
+  constexpr int W = TL::W, NT = TL::NT;
+  extern __shared__ __align__(16) double sm[];
+  double* s_uin = sm + TL::kUin;
+  double* s_un = sm + TL::kUn;
+  const int tid = threadIdx.x;
+  Ctl* ctl = p.a[0].ctl;
+  const long long n = p.a[0].n, pitch = p.a[0].pitch;
+  const long long j0 = (long long)blockIdx.x * T;
+  const int Tc = (int)((n - j0 < T) ? (n - j0) : T);
+  const int cells = Tc + 2 * G;
+  const bool first = blockIdx.x == 0;
+  unsigned long long nbar = 0;
+  const unsigned long long nblk = gridDim.x;
+
+  // window of u^n: stage input and u^n
+  for (int idx = tid; idx < M * cells; idx += NT) {
+    const int c = idx / cells, k = idx - c * cells;
+    const double v = __ldcg(p.a[0].uin + c * pitch + j0 + k);
+    s_uin[c * W + k] = v;
+    s_un[c * W + k] = v;
+  }
+  const double t_final = __ldcg(&ctl->t_final), cfl = __ldcg(&ctl->cfl), dt_fixed = __ldcg(&ctl->dt_fixed);
+  double t = __ldcg(&ctl->t);
+  // status as it stands before any block of this launch can flag a failure
+  bool stop = __ldcg(&ctl->status) != 0;
+  if (!grid_barrier(&ctl->gbar, (++nbar) * nblk)) {
+    if (tid == 0) flag_error(ctl, WT_ERR_TIMEOUT);
+    return;
+  }
+
+  for (long long step = 0; step < p.n_steps; ++step) {
+    if (stop || !(t < t_final)) break;
+    double alpha[M];
+    double dt;
+    // ---- RK1 (alphas of u^n in slot 0)
+#pragma unroll
+    for (int s = 0; s < M; ++s) alpha[s] = bits_to_double(__ldcg(&ctl->amax[0][s]));
+    {
+      const double smax = (FLUX == WT_FLUX_EULER1D) ? ((alpha[0] < alpha[M - 1]) ? alpha[M - 1] : alpha[0]) : alpha[0];
+      dt = dt_fixed > 0.0 ? dt_fixed : MATH::cfl_dt(cfl, p.a[0].dx, smax);
+      const double rem = t_final - t;
+      if (rem < dt) dt = rem;
+    }
+    if (first && tid < 8) ctl->amax[2][tid] = 0ull;
+    if (first && tid == 0) ctl->dt = dt;
+    stage1d_compute<MATH, FLUX, STAGE_RK1, T, kResident>(p.a[0], j0, Tc, 0, j0, j0 + Tc, alpha, dt, sm,
+                                                         AlphaWait{0ull, 0, -1});
+    if (!grid_barrier(&ctl->gbar, (++nbar) * nblk)) {
+      if (tid == 0) flag_error(ctl, WT_ERR_TIMEOUT);
+      return;
+    }
+    load_halos<MATH, FLUX, T>(p.a[1].uin, pitch, j0, Tc, s_uin);
+    // ---- RK2
+#pragma unroll
+    for (int s = 0; s < M; ++s) alpha[s] = bits_to_double(__ldcg(&ctl->amax[1][s]));
+    if (first && tid < 8) ctl->amax[0][tid] = 0ull;
+    stage1d_compute<MATH, FLUX, STAGE_RK2, T, kResident>(p.a[1], j0, Tc, 0, j0, j0 + Tc, alpha, dt, sm,
+                                                         AlphaWait{0ull, 0, -1});
+    if (!grid_barrier(&ctl->gbar, (++nbar) * nblk)) {
+      if (tid == 0) flag_error(ctl, WT_ERR_TIMEOUT);
+      return;
+    }
+    load_halos<MATH, FLUX, T>(p.a[2].uin, pitch, j0, Tc, s_uin);
+    // ---- RK3
+#pragma unroll
+    for (int s = 0; s < M; ++s) alpha[s] = bits_to_double(__ldcg(&ctl->amax[2][s]));
+    if (first && tid < 8) ctl->amax[1][tid] = 0ull;
+    stage1d_compute<MATH, FLUX, STAGE_RK3, T, kResident>(p.a[2], j0, Tc, 0, j0, j0 + Tc, alpha, dt, sm,
+                                                         AlphaWait{0ull, 0, -1});
+    t = t + dt;
+    const int v = (int)(step % 3);
+    if (tid == 0) {
+      if (first) {
+        ctl->t = t;
+        ctl->steps = ctl->steps + 1;
+      }
+      if (__ldcg(&ctl->status) != 0) atomicOr(&ctl->vote[v], 1u);
+    }
+    if (!grid_barrier(&ctl->gbar, (++nbar) * nblk)) {
+      if (tid == 0) flag_error(ctl, WT_ERR_TIMEOUT);
+      return;
+    }
+    stop = __ldcg(&ctl->vote[v]) != 0;
+    if (first && tid == 0) ctl->vote[(v + 2) % 3] = 0u;
+    load_halos<MATH, FLUX, T>(p.a[0].uin, pitch, j0, Tc, s_uin);
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Step-blocked persistent RK3 integration: one CTA per tile of T cells, on at most one tile
+// per SM.  At the start of a step each CTA holds u^n over its cells and 9 halo cells per
+// side (3 per stage); it computes stage 1 over its cells and 6 halo cells per side, stage 2
+// over 3 per side and stage 3 over its own cells, so the only exchange between neighbours
+// is the halo reload at the start of a step.  The halo cells are computed with exactly the
+// arithmetic, alphas and dt of their owners.  Non-periodic ends: the computed range stops
+// at the boundary and the ghost cells are re-imaged from the new values after each stage.
+// Alphas: each stage folds the wave speeds of the CTA's own cells into the next slot and
+// arrives on the grid counter; the next stage waits for all arrivals only after its alpha-
+// free work (cell quantities, Roe matrices, the (l.f, l.u) products), so the reduction over
+// the grid overlaps that work.  Stop votes and t as in persist1d_kernel.
+// ---------------------------------------------------------------------------------------
+template <class MATH, int FLUX, int T>
+__device__ __forceinline__ void sb_load_window(const double* un, long long pitch, long long n, long long x0, int k_lo,
+                                               int k_hi, bool per_lo, bool per_hi, double* s_uin, double* s_un, int W) {
+  constexpr int M = FluxM<FLUX>::m;
+  const int span = k_hi - k_lo;
+  for (int idx = threadIdx.x; idx < M * span; idx += blockDim.x) {
+    const int c = idx / span, k = k_lo + (idx - c * span);
+    const long long x = x0 + k;
+    long long src;
+    if (x < 0) {
+      if (per_lo) src = ((x % n) + n) % n;
+      else if (x >= -G) src = x;
+      else continue;
+    } else if (x >= n) {
+      if (per_hi) src = x % n;
+      else if (x < n + G) src = x;
+      else continue;
+    } else {
+      src = x;
+    }
+    const double v = __ldcg(un + c * pitch + src + G);
+    s_uin[c * W + k] = v;
+    s_un[c * W + k] = v;
+  }
+}
+
+// ghost cells of a non-periodic end inside the window, re-imaged from the new stage values
+template <int FLUX>
+__device__ __forceinline__ void sb_reimage(int bc_lo, int bc_hi, long long n, long long x0, int wcells, double* s_uin,
+                                           int W) {
+  constexpr int M = FluxM<FLUX>::m;
+  const int tid = threadIdx.x;
+  if (tid < 2 * G * M) {
+    const bool hi = tid >= G * M;
+    const int r = hi ? tid - G * M : tid;
+    const int c = r / G, g = r - c * G;
+    const int bc = hi ? bc_hi : bc_lo;
+    if (bc != WT_BC_PERIODIC) {
+      const long long xg = hi ? n + g : -1 - g;
+      const long long xs = (bc == WT_BC_OUTFLOW) ? (hi ? n - 1 : 0) : (hi ? n - 1 - g : g);
+      const long long pg = xg - x0, ps = xs - x0;
+      if (pg >= 0 && pg < wcells && ps >= 0 && ps < wcells) {
+        const double v = s_uin[c * W + ps];
+        s_uin[c * W + pg] = (bc == WT_BC_REFLECTIVE && c == 1) ? -v : v;
+      }
+    }
+  }
+}
+
+template <class MATH, int FLUX, int T>
+__global__ void __launch_bounds__(Tile1D<T + 4 * G, FluxM<FLUX>::m>::NT) stepblock1d_kernel(const PersistArgs p) {
+  constexpr int M = FluxM<FLUX>::m;
+  constexpr int E0 = 3 * G;   // halo cells per side at the start of a step
+  constexpr int TB = T + 4 * G;  // cells computed in stage 1: T + 2 * (E0 - G)
+  using TL = Tile1D<TB, M>;
+  constexpr int W = TL::W;
+  static_assert(W >= T + 2 * E0, "window of a step");
+  extern __shared__ __align__(16) double sm[];
+  double* s_uin = sm + TL::kUin;
+  double* s_un = sm + TL::kUn;
+  const int tid = threadIdx.x;
+  Ctl* ctl = p.a[0].ctl;
+  const long long n = p.a[0].n, pitch = p.a[0].pitch;
+  const long long j0 = (long long)blockIdx.x * T;
+  const int Tc = (int)((n - j0 < T) ? (n - j0) : T);
+  const long long x0 = j0 - E0;
+  const int wcells = Tc + 2 * E0;
+  const int bc_lo = p.a[0].bc_lo, bc_hi = p.a[0].bc_hi;
+  const bool per_lo = bc_lo == WT_BC_PERIODIC, per_hi = bc_hi == WT_BC_PERIODIC;
+  const bool first = blockIdx.x == 0;
+  const unsigned long long nblk = gridDim.x;
+  unsigned long long* gbar = &ctl->gbar;
+  unsigned long long nbar = 0;
+
+  sb_load_window<MATH, FLUX, T>(p.a[0].uin, pitch, n, x0, 0, wcells, per_lo, per_hi, s_uin, s_un, W);
+  const double t_final = __ldcg(&ctl->t_final), cfl = __ldcg(&ctl->cfl), dt_fixed = __ldcg(&ctl->dt_fixed);
+  double t = __ldcg(&ctl->t);
+  // status as it stands before any block of this launch can flag a failure
+  bool stop = __ldcg(&ctl->status) != 0;
+  grid_arrive(gbar);
+  if (!grid_wait(gbar, (++nbar) * nblk)) {
+    if (tid == 0) flag_error(ctl, WT_ERR_TIMEOUT);
+    return;
+  }
+
+  // computed range of a stage with e halo cells per side, clipped at non-periodic ends
+  auto range = [&](int e, long long& lo, int& Ts, int& off) {
+    long long l = j0 - e, h = j0 + Tc + e;
+    if (!per_lo && l < 0) l = 0;
+    if (!per_hi && h > n) h = n;
+    lo = l;
+    Ts = (int)(h - l);
+    off = (int)(l - G - x0);
+  };
+
+  for (long long step = 0;; ++step) {
+    if (step > 0) {
+      if (step >= p.n_steps) break;
+      // the previous step's last stage: stores of u^n, stop votes, alphas of u^n
+      if (!grid_wait(gbar, nbar * nblk)) {
+        if (tid == 0) flag_error(ctl, WT_ERR_TIMEOUT);
+        return;
+      }
+      const int v = (int)((step - 1) % 3);
+      stop = __ldcg(&ctl->vote[v]) != 0;
+      if (first && tid == 0) ctl->vote[(v + 2) % 3] = 0u;
+    }
+    if (step >= p.n_steps || stop || !(t < t_final)) break;
+    if (step > 0) {
+      sb_load_window<MATH, FLUX, T>(p.a[0].uin, pitch, n, x0, 0, E0, per_lo, per_hi, s_uin, s_un, W);
+      sb_load_window<MATH, FLUX, T>(p.a[0].uin, pitch, n, x0, Tc + E0, wcells, per_lo, per_hi, s_uin, s_un, W);
+    }
+    __syncthreads();
+
+    double alpha[M], dt;
+    long long lo;
+    int Ts, off;
+    // ---- RK1 (alphas of u^n in slot 0)
+#pragma unroll
+    for (int f = 0; f < M; ++f) alpha[f] = bits_to_double(__ldcg(&ctl->amax[0][f]));
+    {
+      const double smax = (FLUX == WT_FLUX_EULER1D) ? ((alpha[0] < alpha[M - 1]) ? alpha[M - 1] : alpha[0]) : alpha[0];
+      dt = dt_fixed > 0.0 ? dt_fixed : MATH::cfl_dt(cfl, p.a[0].dx, smax);
+      const double rem = t_final - t;
+      if (rem < dt) dt = rem;
+    }
+    if (first && tid < 8) ctl->amax[2][tid] = 0ull;
+    if (first && tid == 0) ctl->dt = dt;
+    range(2 * G, lo, Ts, off);
+    stage1d_compute<MATH, FLUX, STAGE_RK1, TB, kStepBlocked>(p.a[0], lo, Ts, off, j0, j0 + Tc, alpha, dt, sm,
+                                                             AlphaWait{0ull, 0, -1});
+    sb_reimage<FLUX>(bc_lo, bc_hi, n, x0, wcells, s_uin, W);
+    grid_arrive(gbar);
+    ++nbar;
+    // ---- RK2 (alphas of u1 in slot 1, awaited after the alpha-free work)
+    range(G, lo, Ts, off);
+    if (!stage1d_compute<MATH, FLUX, STAGE_RK2, TB, kStepBlocked>(p.a[1], lo, Ts, off, j0, j0 + Tc, alpha, dt, sm,
+                                                                  AlphaWait{nbar * nblk, 1, first ? 0 : -1})) {
+      if (tid == 0) flag_error(ctl, WT_ERR_TIMEOUT);
+      return;
+    }
+    sb_reimage<FLUX>(bc_lo, bc_hi, n, x0, wcells, s_uin, W);
+    grid_arrive(gbar);
+    ++nbar;
+    // ---- RK3 (alphas of u2 in slot 2)
+    range(0, lo, Ts, off);
+    if (!stage1d_compute<MATH, FLUX, STAGE_RK3, TB, kStepBlocked>(p.a[2], lo, Ts, off, j0, j0 + Tc, alpha, dt, sm,
+                                                                  AlphaWait{nbar * nblk, 2, first ? 1 : -1})) {
+      if (tid == 0) flag_error(ctl, WT_ERR_TIMEOUT);
+      return;
+    }
+    t = t + dt;
+    if (tid == 0) {
+      if (first) {
+        ctl->t = t;
+        ctl->steps = ctl->steps + 1;
+      }
+      if (__ldcg(&ctl->status) != 0) atomicOr(&ctl->vote[(int)(step % 3)], 1u);
+    }
+    grid_arrive(gbar);
+    ++nbar;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
 // Host-side launchers, instantiated per policy
 // ---------------------------------------------------------------------------------------
 
@@ -409,6 +831,116 @@ cudaError_t launch_stage1d_t(const Stage1DArgs& a, cudaStream_t st) {
   auto kern = stage1d_kernel<MATH, FLUX, STAGE, T>;
   const unsigned grid = (unsigned)((a.n + T - 1) / T);
   return launch_pdl(kern, dim3(grid), dim3(TL::NT), TL::bytes, st, a);
+}
+
+// Cooperative launch of the persistent kernel (grid = number of tiles, all co-resident)
+template <class MATH, int FLUX, int T>
+cudaError_t launch_persist1d_t(const PersistArgs& p, int grid, cudaStream_t st) {
+  using TL = Tile1D<T, FluxM<FLUX>::m>;
+  static_assert(TL::bytes <= 48 * 1024, "tile exceeds the default dynamic shared memory limit");
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(TL::NT);
+  cfg.dynamicSmemBytes = TL::bytes;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, persist1d_kernel<MATH, FLUX, T>, p);
+}
+
+// CTAs of the persistent kernel that fit on the device at once (0: no cooperative launch)
+template <class MATH, int FLUX, int T>
+int persist1d_capacity_t() {
+  using TL = Tile1D<T, FluxM<FLUX>::m>;
+  int dev = 0, sms = 0, coop = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, persist1d_kernel<MATH, FLUX, T>, TL::NT, TL::bytes) !=
+      cudaSuccess)
+    return 0;
+  return per * sms;
+}
+
+// Cooperative launch of the step-blocked kernel (grid = number of tiles of T cells)
+template <class MATH, int FLUX, int T>
+cudaError_t launch_stepblock1d_t(const PersistArgs& p, int grid, cudaStream_t st) {
+  using TL = Tile1D<T + 4 * G, FluxM<FLUX>::m>;
+  static_assert(TL::bytes <= 48 * 1024, "tile exceeds the default dynamic shared memory limit");
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(TL::NT);
+  cfg.dynamicSmemBytes = TL::bytes;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, stepblock1d_kernel<MATH, FLUX, T>, p);
+}
+
+template <class MATH, int FLUX, int T>
+int stepblock1d_capacity_t() {
+  using TL = Tile1D<T + 4 * G, FluxM<FLUX>::m>;
+  int dev = 0, sms = 0, coop = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, stepblock1d_kernel<MATH, FLUX, T>, TL::NT, TL::bytes) !=
+      cudaSuccess)
+    return 0;
+  return per * sms;
+}
+
+template <class MATH>
+int stepblock1d_capacity_policy(int flux) {
+  switch (flux) {
+    case WT_FLUX_EULER1D: return stepblock1d_capacity_t<MATH, WT_FLUX_EULER1D, 27>();
+    case WT_FLUX_ADVECTION: return stepblock1d_capacity_t<MATH, WT_FLUX_ADVECTION, 51>();
+    case WT_FLUX_BURGERS: return stepblock1d_capacity_t<MATH, WT_FLUX_BURGERS, 51>();
+  }
+  return 0;
+}
+
+template <class MATH>
+cudaError_t launch_stepblock1d_policy(int flux, const PersistArgs& p, int grid, cudaStream_t st) {
+  switch (flux) {
+    case WT_FLUX_EULER1D: return launch_stepblock1d_t<MATH, WT_FLUX_EULER1D, 27>(p, grid, st);
+    case WT_FLUX_ADVECTION: return launch_stepblock1d_t<MATH, WT_FLUX_ADVECTION, 51>(p, grid, st);
+    case WT_FLUX_BURGERS: return launch_stepblock1d_t<MATH, WT_FLUX_BURGERS, 51>(p, grid, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// tiles with a persistent kernel: 31 and 63 (Euler), 63 (scalar fluxes); 0 for the others
+template <class MATH>
+int persist1d_capacity_policy(int flux, int tile) {
+  if (flux == WT_FLUX_EULER1D) {
+    if (tile == 31) return persist1d_capacity_t<MATH, WT_FLUX_EULER1D, 31>();
+    if (tile == 63) return persist1d_capacity_t<MATH, WT_FLUX_EULER1D, 63>();
+    return 0;
+  }
+  if (tile != 63) return 0;
+  if (flux == WT_FLUX_ADVECTION) return persist1d_capacity_t<MATH, WT_FLUX_ADVECTION, 63>();
+  if (flux == WT_FLUX_BURGERS) return persist1d_capacity_t<MATH, WT_FLUX_BURGERS, 63>();
+  return 0;
+}
+
+template <class MATH>
+cudaError_t launch_persist1d_policy(int flux, int tile, const PersistArgs& p, int grid, cudaStream_t st) {
+  if (flux == WT_FLUX_EULER1D) {
+    if (tile == 31) return launch_persist1d_t<MATH, WT_FLUX_EULER1D, 31>(p, grid, st);
+    if (tile == 63) return launch_persist1d_t<MATH, WT_FLUX_EULER1D, 63>(p, grid, st);
+    return cudaErrorInvalidValue;
+  }
+  if (tile != 63) return cudaErrorInvalidValue;
+  if (flux == WT_FLUX_ADVECTION) return launch_persist1d_t<MATH, WT_FLUX_ADVECTION, 63>(p, grid, st);
+  if (flux == WT_FLUX_BURGERS) return launch_persist1d_t<MATH, WT_FLUX_BURGERS, 63>(p, grid, st);
+  return cudaErrorInvalidValue;
 }
 
 template <class MATH, int FLUX, int T>

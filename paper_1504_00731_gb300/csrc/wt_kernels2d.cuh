@@ -51,9 +51,9 @@ __global__ void __launch_bounds__(256) alpha2d_kernel(const double* __restrict__
                                                       long long rowp, long long planep, double gamma, double dx,
                                                       double dy, Ctl* ctl, int slot) {
   __shared__ double red[9 * 32];
-  double v[8], q = 0.0;
+  unsigned long long v[8], q = 0ull;
 #pragma unroll
-  for (int s = 0; s < 8; ++s) v[s] = 0.0;
+  for (int s = 0; s < 8; ++s) v[s] = 0ull;
   const long long cells = nx * ny;
   for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < cells;
        k += (long long)gridDim.x * blockDim.x) {
@@ -65,13 +65,13 @@ __global__ void __launch_bounds__(256) alpha2d_kernel(const double* __restrict__
     if (!(isfinite(U[0]) && isfinite(U[1]) && isfinite(U[2]) && isfinite(U[3]))) flag_error(ctl, WT_ERR_NONPHYSICAL);
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
-      v[s] = (v[s] < lx[s]) ? lx[s] : v[s];
-      v[4 + s] = (v[4 + s] < ly[s]) ? ly[s] : v[4 + s];
+      key_max(v[s], lx[s]);
+      key_max(v[4 + s], ly[s]);
     }
-    q = (q < qq) ? qq : q;
+    key_max(q, qq);
   }
   block_max_atomic<8>(v, red, ctl->amax[slot]);
-  double qa[1] = {q};
+  unsigned long long qa[1] = {q};
   block_max_atomic<1>(qa, red + 8 * 32, &ctl->cfl2d[slot]);
 }
 
@@ -285,9 +285,9 @@ __global__ void __launch_bounds__(Tile2D<TX, TY>::NT) stage2d_kernel(const Stage
   __syncthreads();
 
   // ---- E: L = Lx + Ly, RK combine, ghost images, wave speeds of the new state
-  double vmax[8], qmax = 0.0;
+  unsigned long long vmax[8], qmax = 0ull;
 #pragma unroll
-  for (int s = 0; s < 8; ++s) vmax[s] = 0.0;
+  for (int s = 0; s < 8; ++s) vmax[s] = 0ull;
   for (int k = tid; k < tcx * tcy; k += NT) {
     const int r = k / tcx, t = k - r * tcx;
     const long long x = x0 + t, y = y0 + r;
@@ -341,16 +341,16 @@ __global__ void __launch_bounds__(Tile2D<TX, TY>::NT) stage2d_kernel(const Stage
       MATH::euler2d_speeds(uo, a.gamma, a.dx, a.dy, lx, ly, q);
 #pragma unroll
       for (int s = 0; s < 4; ++s) {
-        vmax[s] = (vmax[s] < lx[s]) ? lx[s] : vmax[s];
-        vmax[4 + s] = (vmax[4 + s] < ly[s]) ? ly[s] : vmax[4 + s];
+        key_max(vmax[s], lx[s]);
+        key_max(vmax[4 + s], ly[s]);
       }
-      qmax = (qmax < q) ? q : qmax;
+      key_max(qmax, q);
     }
   }
   if (STAGE != STAGE_RHS) {
     const int nxt = (STAGE + 1) % 3;
     block_max_atomic<8>(vmax, s_red, ctl->amax[nxt]);
-    double qa[1] = {qmax};
+    unsigned long long qa[1] = {qmax};
     block_max_atomic<1>(qa, s_red + 8 * 32, &ctl->cfl2d[nxt]);
     if (STAGE == STAGE_RK3 && first_tile && tid == 0) {
       ctl->t = ctl->t + dt;

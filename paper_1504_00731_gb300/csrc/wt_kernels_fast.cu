@@ -113,6 +113,18 @@ cudaError_t launch_gather_t(const Ctl* ctl, int nprob, double* t_out, cudaStream
   return cudaGetLastError();
 }
 
+cudaError_t launch_persist1d_fast(int flux, int tile, const PersistArgs& p, int grid, cudaStream_t st) {
+  return launch_persist1d_policy<FastMath>(flux, tile, p, grid, st);
+}
+
+int persist1d_capacity_fast(int flux, int tile) { return persist1d_capacity_policy<FastMath>(flux, tile); }
+
+cudaError_t launch_stepblock1d_fast(int flux, const PersistArgs& p, int grid, cudaStream_t st) {
+  return launch_stepblock1d_policy<FastMath>(flux, p, grid, st);
+}
+
+int stepblock1d_capacity_fast(int flux) { return stepblock1d_capacity_policy<FastMath>(flux); }
+
 cudaError_t launch_stage1d_fast(int flux, int stage, int tile, const Stage1DArgs& a, cudaStream_t st) {
   return launch_stage1d_policy<FastMath>(flux, stage, tile, a, st);
 }

@@ -7,6 +7,18 @@
 
 namespace wt {
 
+cudaError_t launch_persist1d_strict(int flux, int tile, const PersistArgs& p, int grid, cudaStream_t st) {
+  return launch_persist1d_policy<StrictMath>(flux, tile, p, grid, st);
+}
+
+int persist1d_capacity_strict(int flux, int tile) { return persist1d_capacity_policy<StrictMath>(flux, tile); }
+
+cudaError_t launch_stepblock1d_strict(int flux, const PersistArgs& p, int grid, cudaStream_t st) {
+  return launch_stepblock1d_policy<StrictMath>(flux, p, grid, st);
+}
+
+int stepblock1d_capacity_strict(int flux) { return stepblock1d_capacity_policy<StrictMath>(flux); }
+
 cudaError_t launch_stage1d_strict(int flux, int stage, int tile, const Stage1DArgs& a, cudaStream_t st) {
   return launch_stage1d_policy<StrictMath>(flux, stage, tile, a, st);
 }

@@ -24,6 +24,12 @@ struct Stage1DArgs {
   Ctl* ctl;
 };
 
+// Arguments of the persistent kernel: the three stages of an RK step and the steps to take
+struct PersistArgs {
+  Stage1DArgs a[3];
+  long long n_steps;
+};
+
 // One problem of a batch: padded storage at poff in the workspace planes, caller storage
 // at uoff in the caller's packed planes.
 struct BatchSeg {
@@ -143,6 +149,17 @@ int adj_tile_width();
 // Records a message for wt_last_error() on the calling thread and returns code.
 int set_last_error(int code, const char* msg);
 
+cudaError_t launch_persist1d_strict(int flux, int tile, const PersistArgs& p, int grid, cudaStream_t st);
+cudaError_t launch_persist1d_fast(int flux, int tile, const PersistArgs& p, int grid, cudaStream_t st);
+int persist1d_capacity_strict(int flux, int tile);
+// tile of the step-blocked kernel: 27 cells (Euler: 3 x 40 interface items = 4 warps in stage
+// 1), 51 cells (scalar fluxes: 64 items = 2 warps)
+inline int stepblock1d_tile(int flux) { return flux == WT_FLUX_EULER1D ? 27 : 51; }
+cudaError_t launch_stepblock1d_strict(int flux, const PersistArgs& p, int grid, cudaStream_t st);
+cudaError_t launch_stepblock1d_fast(int flux, const PersistArgs& p, int grid, cudaStream_t st);
+int stepblock1d_capacity_strict(int flux);
+int stepblock1d_capacity_fast(int flux);
+int persist1d_capacity_fast(int flux, int tile);
 cudaError_t launch_stage1d_strict(int flux, int stage, int tile, const Stage1DArgs& a, cudaStream_t st);
 cudaError_t launch_stage1d_fast(int flux, int stage, int tile, const Stage1DArgs& a, cudaStream_t st);
 cudaError_t launch_alpha1d_strict(int flux, const double* u, long long n, long long pitch, double gamma, double adv,

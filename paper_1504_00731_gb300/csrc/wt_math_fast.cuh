@@ -95,9 +95,42 @@ struct FastMath {
     vp = fma(alpha, hu, 0.5 * f);
     vm = fma(-alpha, hu, 0.5 * f);
   }
+  // the same projections in two parts: (a, b) = (l.f, l.u) before alpha is known, then v+-
+  __device__ __forceinline__ static void project3_ab(const double* l, const double* f, const double* U, double& a,
+                                                     double& b) {
+    a = fma(l[2], f[2], fma(l[1], f[1], l[0] * f[0]));
+    b = fma(l[2], U[2], fma(l[1], U[1], l[0] * U[0]));
+  }
+  __device__ __forceinline__ static void project1_ab(double f, double u, double& a, double& b) {
+    a = 0.5 * f;
+    b = 0.5 * u;
+  }
+  __device__ __forceinline__ static void project_v(double a, double b, double alpha, double& vp, double& vm) {
+    vp = fma(alpha, b, a);
+    vm = fma(-alpha, b, a);
+  }
 
-  __device__ __forceinline__ static double weno_flags(const double* q, double eps, double alpha_R, bool& restricted_out,
-                                                    bool& theta1_out) {
+  // The reconstruction in two parts.  weno_begin evaluates the sub-stencil values, the
+  // indicators, tau and the theta switch; a restricted stencil (Eq. (be_res)) finishes there
+  // with the linear combination (returns true, value in out).  Otherwise the nonlinear
+  // weights of Eq. (om) are left to weno_finish, which needs only the record w.
+  static constexpr bool kSplitWeno = true;
+  struct WenoPart {
+    double e[4];   // eps + beta_k
+    double tau;    // tau^theta
+    double fh[4];  // sub-stencil values
+    bool theta1;
+  };
+
+  __device__ __forceinline__ static void gammas(bool theta1, double& g0, double& g1, double& g2, double& g3) {
+    g0 = theta1 ? 2.0 / 20.0 : 1.0 / 20.0;
+    g1 = theta1 ? 12.0 / 20.0 : 9.0 / 20.0;
+    g2 = theta1 ? 6.0 / 20.0 : 9.0 / 20.0;
+    g3 = theta1 ? 0.0 : 1.0 / 20.0;
+  }
+
+  __device__ __forceinline__ static bool weno_begin(const double* q, double eps, double alpha_R, double& out,
+                                                    WenoPart& w) {
     constexpr double C1312 = 13.0 / 12.0, C1348 = 13.0 / 48.0;
     const double d0 = q[1] - q[0], d1 = q[2] - q[1], d2 = q[3] - q[2], d3 = q[4] - q[3], d4 = q[5] - q[4];
     const double s0 = d1 - d0, s1 = d2 - d1, s2 = d3 - d2, s3 = d4 - d3;
@@ -118,33 +151,49 @@ struct FastMath {
     const double tau5 = fma(C1312 * t5a, t5a, t5b * t5b);
     const double tau6 = fma(C1312 * t6a, t6a, 0.25 * (t6b * t6b));
     // Eqs. (fh0)-(fh3) in difference form
-    const double fh0 = fma(5.0 / 6.0, d1, fma(-1.0 / 3.0, d0, q[2]));
-    const double fh1 = fma(1.0 / 6.0, d1, fma(1.0 / 3.0, d2, q[2]));
-    const double fh2 = fma(2.0 / 3.0, d2, fma(-1.0 / 6.0, d3, q[2]));
-    const double fh3 = fma(1.0 / 3.0, d4, fma(-5.0 / 6.0, d3, q[3]));
-    // Eq. (tau_we6) and Eq. (gam_we6)
-    const bool theta1 = !(bits(tau6) < bits(tau5));
-    const double tau = theta1 ? tau5 : tau6;
-    const double g0 = theta1 ? 2.0 / 20.0 : 1.0 / 20.0;
-    const double g1 = theta1 ? 12.0 / 20.0 : 9.0 / 20.0;
-    const double g2 = theta1 ? 6.0 / 20.0 : 9.0 / 20.0;
-    const double g3w = theta1 ? 0.0 : 1.0 / 20.0;
+    w.fh[0] = fma(5.0 / 6.0, d1, fma(-1.0 / 3.0, d0, q[2]));
+    w.fh[1] = fma(1.0 / 6.0, d1, fma(1.0 / 3.0, d2, q[2]));
+    w.fh[2] = fma(2.0 / 3.0, d2, fma(-1.0 / 6.0, d3, q[2]));
+    w.fh[3] = fma(1.0 / 3.0, d4, fma(-5.0 / 6.0, d3, q[3]));
+    // Eq. (tau_we6)
+    w.theta1 = !(bits(tau6) < bits(tau5));
+    w.tau = w.theta1 ? tau5 : tau6;
     // Eq. (be_res)
     const double bmax = nmax(nmax(b0, b1), nmax(b2, b3));
     const double bmin = nmin(nmin(b0, b1), nmin(b2, b3));
-    const bool restricted = !(bits(fma(alpha_R, bmin, alpha_R * eps)) < bits(bmax));
-    restricted_out = restricted;
-    theta1_out = theta1;
-    if (restricted) return fma(g3w, fh3, fma(g2, fh2, fma(g1, fh1, g0 * fh0)));
-    // Eq. (om) over the common denominator prod_l (eps + beta_l)
-    const double e0d = eps + b0, e1d = eps + b1, e2d = eps + b2, e3d = eps + b3;
-    const double p01 = e0d * e1d, p23 = e2d * e3d;
-    const double w0 = g0 * (e0d + tau) * (e1d * p23);
-    const double w1 = g1 * (e1d + tau) * (e0d * p23);
-    const double w2 = g2 * (e2d + tau) * (p01 * e3d);
-    const double w3 = g3w * (e3d + tau) * (p01 * e2d);
-    const double num = fma(w3, fh3, fma(w2, fh2, fma(w1, fh1, w0 * fh0)));
+    if (!(bits(fma(alpha_R, bmin, alpha_R * eps)) < bits(bmax))) {
+      double c0, c1, c2, c3;  // Eq. (gam_we6)
+      gammas(w.theta1, c0, c1, c2, c3);
+      out = fma(c3, w.fh[3], fma(c2, w.fh[2], fma(c1, w.fh[1], c0 * w.fh[0])));
+      return true;
+    }
+    w.e[0] = eps + b0;
+    w.e[1] = eps + b1;
+    w.e[2] = eps + b2;
+    w.e[3] = eps + b3;
+    return false;
+  }
+
+  // Eq. (om) over the common denominator prod_l (eps + beta_l)
+  __device__ __forceinline__ static double weno_finish(const WenoPart& w) {
+    double g0, g1, g2, g3;
+    gammas(w.theta1, g0, g1, g2, g3);
+    const double p01 = w.e[0] * w.e[1], p23 = w.e[2] * w.e[3];
+    const double w0 = g0 * (w.e[0] + w.tau) * (w.e[1] * p23);
+    const double w1 = g1 * (w.e[1] + w.tau) * (w.e[0] * p23);
+    const double w2 = g2 * (w.e[2] + w.tau) * (p01 * w.e[3]);
+    const double w3 = g3 * (w.e[3] + w.tau) * (p01 * w.e[2]);
+    const double num = fma(w3, w.fh[3], fma(w2, w.fh[2], fma(w1, w.fh[1], w0 * w.fh[0])));
     return num / ((w0 + w1) + (w2 + w3));
+  }
+
+  __device__ __forceinline__ static double weno_flags(const double* q, double eps, double alpha_R, bool& restricted_out,
+                                                    bool& theta1_out) {
+    WenoPart w;
+    double out;
+    restricted_out = weno_begin(q, eps, alpha_R, out, w);
+    theta1_out = w.theta1;
+    return restricted_out ? out : weno_finish(w);
   }
 
   __device__ __forceinline__ static double weno(const double* q, double eps, double alpha_R) {

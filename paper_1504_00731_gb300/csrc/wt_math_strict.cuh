@@ -12,6 +12,14 @@ struct StrictMath {
   static constexpr bool kStrict = true;
   // projection v = kProj (L f +- alpha L u) with the stored L = kLScale * L_true
   static constexpr double kProj = 0.5, kLScale = 1.0;
+  // the reconstruction is evaluated in one piece (weno_flags)
+  static constexpr bool kSplitWeno = false;
+  struct WenoPart {
+    double e[4], tau, fh[4];
+    bool theta1;
+  };
+  __device__ __forceinline__ static bool weno_begin(const double*, double, double, double&, WenoPart&) { return true; }
+  __device__ __forceinline__ static double weno_finish(const WenoPart&) { return 0.0; }
 
   // ---- scalar fluxes (Eq. (lin_eq), Eq. (bur_eq))
   __device__ __forceinline__ static double flux_advection(double a, double u) { return a * u; }
@@ -79,6 +87,24 @@ struct StrictMath {
   __device__ __forceinline__ static void project1(double f, double u, double alpha, double& vp, double& vm) {
     vp = 0.5 * (f + alpha * u);
     vm = 0.5 * (f - alpha * u);
+  }
+  // the same projections in two parts: (a, b) = (l.f, l.u) before alpha is known, then v+-
+  __device__ __forceinline__ static void project3_ab(const double* l, const double* f, const double* U, double& a,
+                                                     double& b) {
+    a = l[0] * f[0];
+    b = l[0] * U[0];
+    a = a + l[1] * f[1];
+    b = b + l[1] * U[1];
+    a = a + l[2] * f[2];
+    b = b + l[2] * U[2];
+  }
+  __device__ __forceinline__ static void project1_ab(double f, double u, double& a, double& b) {
+    a = f;
+    b = u;
+  }
+  __device__ __forceinline__ static void project_v(double a, double b, double alpha, double& vp, double& vm) {
+    vp = 0.5 * (a + alpha * b);
+    vm = 0.5 * (a - alpha * b);
   }
 
   // ---- WENO-theta interface value, Eqs. (fh0)-(fh3), (be0_cen)-(be3_cen), (be_res),

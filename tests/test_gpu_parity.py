@@ -150,6 +150,73 @@ def test_euler_run_strict_bitwise(wtlib, oracle):
         assert np.array_equal(u, ref), np.abs(u - ref).max()
 
 
+def test_all_launch_strategies_are_bitwise(wtlib, oracle):
+    """The step entry point picks its launch by how the grid's tiles fit on the device: the
+    step-blocked persistent kernel (at most one tile per SM: up to 4104 Euler / 7752 scalar
+    cells), the persistent kernel with a halo exchange per stage (all tiles co-resident), or
+    CUDA graphs of the stage kernels.  All three are bitwise equal to the oracle in strict mode."""
+    b, O = wtlib, oracle
+    cases = ((2, 2000, 1), (2, 4104, 0), (2, 20000, 1), (2, 40000, 1),
+             (0, 1000, 0), (0, 10000, 0), (0, 20000, 0), (1, 7000, 1))
+    for flux, n, bc in cases:
+        steps = 4
+        if flux == 2:
+            U, x, dx = W.euler_riemann(n, W.riemann_params(n), periodic=bc == 0)
+            lo, hi = -5.0, 5.0
+        else:
+            U, _, _ = W.advection_ic2(n, 2)
+            if flux == 1:
+                U = U + 0.5
+            lo, hi = -1.0, 1.0
+            dx = (hi - lo) / n
+        prob = b.problem(flux, bc=bc, mode=b.WT_MODE_STRICT)
+        u, t, s = _gpu_run(b, prob, U, lo, hi, cfl=0.5, max_steps=steps)
+        ref, t_ref, s_ref = O.run(_oracle_problem(O, b, prob), U, dx, cfl=0.5, n_steps=steps)
+        assert s == s_ref == steps and t == t_ref, (flux, n)
+        assert np.array_equal(u, ref), (flux, n, np.abs(u - ref).max())
+
+
+@pytest.mark.parametrize("bc", [0, 1, 2], ids=["periodic", "outflow", "reflective"])
+def test_tiny_and_ragged_grids_run_bitwise(wtlib, oracle, bc):
+    """Grids shorter than the 9 halo cells a step-blocked tile carries per side, and ragged
+    last tiles (1, 2, 8, 9 and 26 cells), for every boundary condition, 6 steps."""
+    b, O = wtlib, oracle
+    for n in (3, 4, 5, 8, 9, 10, 17, 28, 29, 35, 36, 54, 80):
+        U, x, dx = W.euler_riemann(n, W.riemann_params(n + 7), periodic=bc == 0)
+        prob = b.problem(b.WT_FLUX_EULER1D, bc=bc, mode=b.WT_MODE_STRICT, alpha_R=W.ALPHA_R_SEEDED)
+        ref, t_ref, s_ref = O.run(_oracle_problem(O, b, prob), U, dx, cfl=0.5, n_steps=6)
+        if not np.isfinite(ref).all():
+            # the oracle's state blows up too (periodic n = 4): the GPU path must report it
+            with pytest.raises(b.WenoThetaError) as e:
+                _gpu_run(b, prob, U, -5.0, 5.0, cfl=0.5, max_steps=6)
+            assert e.value.status == b.WT_ERR_NONPHYSICAL
+            continue
+        u, t, s = _gpu_run(b, prob, U, -5.0, 5.0, cfl=0.5, max_steps=6)
+        assert s == s_ref == 6 and t == t_ref, n
+        assert np.array_equal(u, ref), (n, np.abs(u - ref).max())
+        if bc == 2:
+            continue  # reflective walls are defined for the Euler equations only
+        V, _, _ = W.advection_ic2(n, 2)
+        pa = b.problem(b.WT_FLUX_BURGERS, bc=bc, mode=b.WT_MODE_STRICT)
+        V = V + 0.3
+        u, t, s = _gpu_run(b, pa, V, -1.0, 1.0, cfl=0.5, max_steps=6)
+        ref, t_ref, s_ref = O.run(_oracle_problem(O, b, pa), V, 2.0 / n, cfl=0.5, n_steps=6)
+        assert s == s_ref == 6 and t == t_ref, n
+        assert np.array_equal(u, ref), (n, np.abs(u - ref).max())
+
+
+def test_persistent_run_across_launch_chunks(wtlib, oracle):
+    """More steps than one persistent launch takes (4096): the run resumes across launches
+    with the same alpha slots and time, bit for bit."""
+    b, O = wtlib, oracle
+    U, _, _ = W.advection_ic2(64, 2)
+    prob = b.problem(b.WT_FLUX_ADVECTION, bc=b.WT_BC_PERIODIC, mode=b.WT_MODE_STRICT)
+    u, t, s = _gpu_run(b, prob, U, -1.0, 1.0, cfl=0.4, max_steps=4100)
+    ref, t_ref, s_ref = O.run(_oracle_problem(O, b, prob), U, 2.0 / 64, cfl=0.4, n_steps=4100)
+    assert s == s_ref == 4100 and t == t_ref
+    assert np.array_equal(u, ref)
+
+
 def test_euler_run_to_final_time(wtlib, oracle):
     """t_final-bounded run: the last step is clipped and the run stops exactly at t_final."""
     b, O = wtlib, oracle
