@@ -140,6 +140,14 @@ __device__ __forceinline__ void block_max_atomic(unsigned long long (&v)[K], dou
   }
 }
 
+// Named CTA barrier `id` over `count` threads: arrive without waiting, or arrive and wait
+__device__ __forceinline__ void named_barrier_arrive(int id, int count) {
+  asm volatile("barrier.cta.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ void named_barrier_sync(int id, int count) {
+  asm volatile("barrier.cta.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
 // ---------------------------------------------------------------------------------------
 // Grid-wide barrier of a cooperative (co-resident) grid.  ctr counts arrivals from 0 at the
 // launch; the k-th barrier of the launch (k = 1, 2, ...) waits for k * gridDim.x of them.

@@ -136,20 +136,26 @@ enum { kStage = 0, kResident = 1, kStepBlocked = 2 };
 
 // Alphas of the stage still to be produced by the other CTAs: wait for `target` arrivals on
 // ctl->gbar (target 0: the alphas are given), then read ctl->amax[slot]; the CTA with
-// clear >= 0 then zeroes that slot of the ring.
+// clear >= 0 then zeroes that slot of the ring.  first_stage: the stage opens an RK step,
+// whose dt (from these alphas, cfl or dt_fixed, clipped at t_final) is set after the wait.
 struct AlphaWait {
   unsigned long long target;
   int slot, clear;
+  int first_stage;
+  double cfl, dt_fixed, t, t_final;
 };
 
 // Phases B-E of one stage over the cells [js, js + Ts) whose window [js - 3, js + Ts + 3) is
-// in shared memory at s_uin[off...] (s_un for stages 2 and 3), with the stage's dt.  Ends
-// with the block's wave-speed maxima (cells of [own_lo, own_hi)) folded into the next alpha
-// slot.  Returns false if a wait for the alphas timed out.
+// in shared memory at s_uin[off...] (s_un for stages 2 and 3), with the stage's dt.  The
+// wave speeds of the cells of [own_lo, own_hi) go to the alpha ring: in kStage and kResident
+// those of the stage output (phase E, next slot, atomics at the end of the stage); in
+// kStepBlocked those of the stage input (phase B, this stage's slot, then an arrival on the
+// grid counter by the last warp while the others go on).  Returns false if a wait for the
+// alphas timed out.
 template <class MATH, int FLUX, int STAGE, int T, int MODE>
 __device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long long js, const int Ts, const int off,
                                                 const long long own_lo, const long long own_hi,
-                                                double (&alpha)[FluxM<FLUX>::m], const double dt, double* sm,
+                                                double (&alpha)[FluxM<FLUX>::m], double& dt, double* sm,
                                                 const AlphaWait aw) {
   constexpr int M = FluxM<FLUX>::m;
   using TL = Tile1D<T, M>;
@@ -174,27 +180,102 @@ __device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long
   const int cells = Tc + 2 * G;
   constexpr bool kNeedUn = (STAGE == STAGE_RK2 || STAGE == STAGE_RK3);
 
-  // ---- B: per-cell quantities
+  // ---- B: per-cell quantities (step-blocked: also ghost images of the stage input).
+  // Step-blocked: the last warp meanwhile takes the wave speeds of the CTA's own cells, folds
+  // their maxima into this stage's alpha slot, arrives on the grid counter, waits for every
+  // CTA's arrival and leaves the alphas in shared memory (s_alpha, s_aflag), all before the
+  // end of phase C0.  Its lanes release the other warps from phase B first (named barrier 1).
+  constexpr int kSW = NT / 32 - 1;  // the speed warp (step-blocked)
+  unsigned long long* s_alpha = reinterpret_cast<unsigned long long*>(s_red);
+  int* s_aflag = reinterpret_cast<int*>(sm + TL::kQn) + 1;
   if (tid == 0) *reinterpret_cast<int*>(sm + TL::kQn) = 0;
-  for (int k = tid; k < cells; k += NT) {
-    if (FLUX == WT_FLUX_EULER1D) {
-      double U[3] = {s_uin[off + k], s_uin[W + off + k], s_uin[2 * W + off + k]};
-      double f[3], u, H, sr, p;
-      MATH::euler_cell(U, a.gamma, f, u, H, sr, p);
-      if (!finite3(U)) flag_error(ctl, WT_ERR_NONPHYSICAL);
-      s_f[k] = f[0];
-      s_f[W + k] = f[1];
-      s_f[2 * W + k] = f[2];
-      s_vel[k] = u;
-      s_H[k] = H;
-      s_sr[k] = sr;
-    } else {
-      const double x = s_uin[off + k];
-      if (!isfinite(x)) flag_error(ctl, WT_ERR_NONPHYSICAL);
-      s_f[k] = (FLUX == WT_FLUX_ADVECTION) ? MATH::flux_advection(a.adv_speed, x) : MATH::flux_burgers(x);
+  if (MODE == kStepBlocked && (tid >> 5) == kSW) {
+    const int lane = tid & 31;
+    unsigned long long vb[M];
+#pragma unroll
+    for (int f = 0; f < M; ++f) vb[f] = 0ull;
+    const int own0 = off + (int)(own_lo - js) + G;  // window position of the first own cell
+    const int nown = (int)(own_hi - own_lo);
+    for (int q = lane; q < nown; q += 32) {
+      double U[M];
+#pragma unroll
+      for (int c = 0; c < M; ++c) U[c] = s_uin[c * W + own0 + q];
+      if (FLUX == WT_FLUX_EULER1D) {
+        double lam[3];
+        MATH::euler_speeds(U, a.gamma, lam);
+#pragma unroll
+        for (int f = 0; f < M; ++f) key_max(vb[f], lam[f]);
+      } else {
+        key_max(vb[0], (FLUX == WT_FLUX_ADVECTION) ? fabs(a.adv_speed) : fabs(U[0]));
+      }
     }
+#pragma unroll
+    for (int f = 0; f < M; ++f) vb[f] = warp_max_key(vb[f]);
+    named_barrier_arrive(1, NT);
+    if (lane == 0) {
+#pragma unroll
+      for (int f = 0; f < M; ++f) atomicMax(&ctl->amax[STAGE][f], vb[f]);
+      __threadfence();
+      atomicAdd(&ctl->gbar, 1ull);
+      const long long start = clock64();
+      int ok = 1;
+      while (ld_acquire_u64(&ctl->gbar) < aw.target) {
+        if (clock64() - start > (1LL << 31)) {
+          ok = 0;
+          break;
+        }
+      }
+      if (ok) {
+#pragma unroll
+        for (int f = 0; f < M; ++f) s_alpha[f] = __ldcg(&ctl->amax[STAGE][f]);
+        if (aw.clear >= 0)
+          for (int e = 0; e < 8; ++e) ctl->amax[aw.clear][e] = 0ull;
+      }
+      *s_aflag = ok ? 1 : 2;
+    }
+  } else {
+    const int nb = (MODE == kStepBlocked) ? NT - 32 : NT;  // threads of phase B
+    for (int k = tid; k < cells; k += nb) {
+      double U[M];
+#pragma unroll
+      for (int c = 0; c < M; ++c) U[c] = s_uin[c * W + off + k];
+      if (MODE == kStepBlocked) {
+        // a ghost cell of a non-periodic end takes the image of the stage input
+        const long long x = js - G + k;
+        const bool lo_g = x < 0 && a.bc_lo != WT_BC_PERIODIC, hi_g = x >= n && a.bc_hi != WT_BC_PERIODIC;
+        if (lo_g || hi_g) {
+          const int bc = hi_g ? a.bc_hi : a.bc_lo;
+          const long long xs = (bc == WT_BC_OUTFLOW) ? (hi_g ? n - 1 : 0) : (hi_g ? 2 * n - 1 - x : -1 - x);
+          const int ks = k + (int)(xs - x);
+#pragma unroll
+          for (int c = 0; c < M; ++c) {
+            const double v = s_uin[c * W + off + ks];
+            U[c] = (bc == WT_BC_REFLECTIVE && c == 1) ? -v : v;
+            s_uin[c * W + off + k] = U[c];
+          }
+        }
+      }
+      if (FLUX == WT_FLUX_EULER1D) {
+        double f[3], u, H, sr, p;
+        MATH::euler_cell(U, a.gamma, f, u, H, sr, p);
+        if (!finite3(U)) flag_error(ctl, WT_ERR_NONPHYSICAL);
+        s_f[k] = f[0];
+        s_f[W + k] = f[1];
+        s_f[2 * W + k] = f[2];
+        s_vel[k] = u;
+        s_H[k] = H;
+        s_sr[k] = sr;
+      } else {
+        const double xv = U[0];
+        if (!isfinite(xv)) flag_error(ctl, WT_ERR_NONPHYSICAL);
+        s_f[k] = (FLUX == WT_FLUX_ADVECTION) ? MATH::flux_advection(a.adv_speed, xv) : MATH::flux_burgers(xv);
+      }
+    }
+    if (MODE == kStepBlocked) named_barrier_sync(1, NT);
   }
-  __syncthreads();
+  if (MODE != kStepBlocked) __syncthreads();
+  // step-blocked scalar fluxes have no phase C0: the alphas are awaited here
+  if (MODE == kStepBlocked && FLUX != WT_FLUX_EULER1D) __syncthreads();
 
   // ---- C0: Roe average and left eigenvectors per interface (interface i: cells i+2 | i+3)
   if (FLUX == WT_FLUX_EULER1D) {
@@ -237,11 +318,18 @@ __device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long
       for (int kk = 0; kk < 6; ++kk) MATH::project1_ab(s_f[i + kk], s_uin[off + i + kk], pa[kk], pb[kk]);
     }
   }
-  if (MODE == kStepBlocked && aw.target != 0ull) {
-    if (!grid_wait(&ctl->gbar, aw.target)) return false;
+  if (MODE == kStepBlocked) {
+    // the speed warp finished before the end of phase C0 (or the barrier after phase B)
+    if (*s_aflag != 1) return false;
 #pragma unroll
-    for (int f = 0; f < M; ++f) alpha[f] = bits_to_double(__ldcg(&ctl->amax[aw.slot][f]));
-    if (aw.clear >= 0 && tid < 8) ctl->amax[aw.clear][tid] = 0ull;
+    for (int f = 0; f < M; ++f) alpha[f] = bits_to_double(s_alpha[f]);
+    if (aw.first_stage) {
+      const double smax = (FLUX == WT_FLUX_EULER1D) ? ((alpha[0] < alpha[M - 1]) ? alpha[M - 1] : alpha[0]) : alpha[0];
+      dt = aw.dt_fixed > 0.0 ? aw.dt_fixed : MATH::cfl_dt(aw.cfl, a.dx, smax);
+      const double rem = aw.t_final - aw.t;
+      if (rem < dt) dt = rem;
+      if (aw.clear >= 0 && tid == 0) ctl->dt = dt;
+    }
   }
   if (has_item) {
     const double al = (s == 0) ? alpha[0] : ((s == 1) ? alpha[1] : alpha[M - 1]);
@@ -361,7 +449,9 @@ __device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long
           }
         }
       }
-      if (own) {
+      if (own && MODE == kStepBlocked) {
+        if (FLUX == WT_FLUX_EULER1D ? !finite3(uo) : !isfinite(uo[0])) flag_error(ctl, WT_ERR_NONPHYSICAL);
+      } else if (own) {
         if (FLUX == WT_FLUX_EULER1D) {
           double lam[3];
           MATH::euler_speeds(uo, a.gamma, lam);
@@ -376,7 +466,11 @@ __device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long
       }
     }
   }
-  if (STAGE != STAGE_RHS) block_max_atomic<M>(vmax, s_red, ctl->amax[(STAGE + 1) % 3]);
+  if (MODE == kStepBlocked) {
+    __syncthreads();
+  } else if (STAGE != STAGE_RHS) {
+    block_max_atomic<M>(vmax, s_red, ctl->amax[(STAGE + 1) % 3]);
+  }
   return true;
 }
 
@@ -451,7 +545,8 @@ __device__ __forceinline__ bool stage1d_tile(const Stage1DArgs& a, const long lo
     ctl->active = 1;
   }
 
-  stage1d_compute<MATH, FLUX, STAGE, T, kStage>(a, j0, Tc, off, j0, j0 + Tc, alpha, dt, sm, AlphaWait{0ull, 0, -1});
+  stage1d_compute<MATH, FLUX, STAGE, T, kStage>(a, j0, Tc, off, j0, j0 + Tc, alpha, dt, sm,
+                                                AlphaWait{0ull, 0, -1, 0, 0.0, 0.0, 0.0, 0.0});
   if (STAGE != STAGE_RHS) {
     if (STAGE == STAGE_RK3 && first_tile && tid == 0) {
       ctl->t = ctl->t + dt;
@@ -585,7 +680,7 @@ __global__ void __launch_bounds__(Tile1D<T, FluxM<FLUX>::m>::NT) persist1d_kerne
     if (first && tid < 8) ctl->amax[2][tid] = 0ull;
     if (first && tid == 0) ctl->dt = dt;
     stage1d_compute<MATH, FLUX, STAGE_RK1, T, kResident>(p.a[0], j0, Tc, 0, j0, j0 + Tc, alpha, dt, sm,
-                                                         AlphaWait{0ull, 0, -1});
+                                                         AlphaWait{0ull, 0, -1, 0, 0.0, 0.0, 0.0, 0.0});
     if (!grid_barrier(&ctl->gbar, (++nbar) * nblk)) {
       if (tid == 0) flag_error(ctl, WT_ERR_TIMEOUT);
       return;
@@ -596,7 +691,7 @@ __global__ void __launch_bounds__(Tile1D<T, FluxM<FLUX>::m>::NT) persist1d_kerne
     for (int s = 0; s < M; ++s) alpha[s] = bits_to_double(__ldcg(&ctl->amax[1][s]));
     if (first && tid < 8) ctl->amax[0][tid] = 0ull;
     stage1d_compute<MATH, FLUX, STAGE_RK2, T, kResident>(p.a[1], j0, Tc, 0, j0, j0 + Tc, alpha, dt, sm,
-                                                         AlphaWait{0ull, 0, -1});
+                                                         AlphaWait{0ull, 0, -1, 0, 0.0, 0.0, 0.0, 0.0});
     if (!grid_barrier(&ctl->gbar, (++nbar) * nblk)) {
       if (tid == 0) flag_error(ctl, WT_ERR_TIMEOUT);
       return;
@@ -607,7 +702,7 @@ __global__ void __launch_bounds__(Tile1D<T, FluxM<FLUX>::m>::NT) persist1d_kerne
     for (int s = 0; s < M; ++s) alpha[s] = bits_to_double(__ldcg(&ctl->amax[2][s]));
     if (first && tid < 8) ctl->amax[1][tid] = 0ull;
     stage1d_compute<MATH, FLUX, STAGE_RK3, T, kResident>(p.a[2], j0, Tc, 0, j0, j0 + Tc, alpha, dt, sm,
-                                                         AlphaWait{0ull, 0, -1});
+                                                         AlphaWait{0ull, 0, -1, 0, 0.0, 0.0, 0.0, 0.0});
     t = t + dt;
     const int v = (int)(step % 3);
     if (tid == 0) {
@@ -634,11 +729,12 @@ __global__ void __launch_bounds__(Tile1D<T, FluxM<FLUX>::m>::NT) persist1d_kerne
 // over 3 per side and stage 3 over its own cells, so the only exchange between neighbours
 // is the halo reload at the start of a step.  The halo cells are computed with exactly the
 // arithmetic, alphas and dt of their owners.  Non-periodic ends: the computed range stops
-// at the boundary and the ghost cells are re-imaged from the new values after each stage.
-// Alphas: each stage folds the wave speeds of the CTA's own cells into the next slot and
-// arrives on the grid counter; the next stage waits for all arrivals only after its alpha-
-// free work (cell quantities, Roe matrices, the (l.f, l.u) products), so the reduction over
-// the grid overlaps that work.  Stop votes and t as in persist1d_kernel.
+// at the boundary and phase B re-images the ghost cells from the stage input.
+// Alphas: phase B of each stage folds the wave speeds of the CTA's own cells of the stage
+// input into the stage's slot and arrives on the grid counter; the CTA waits for all
+// arrivals only after its alpha-free work (cell quantities, Roe matrices, the (l.f, l.u)
+// products), so the reduction over the grid overlaps that work.  dt follows from the alphas
+// of the first stage.  Stop votes and t as in persist1d_kernel.
 // ---------------------------------------------------------------------------------------
 template <class MATH, int FLUX, int T>
 __device__ __forceinline__ void sb_load_window(const double* un, long long pitch, long long n, long long x0, int k_lo,
@@ -663,29 +759,6 @@ __device__ __forceinline__ void sb_load_window(const double* un, long long pitch
     const double v = __ldcg(un + c * pitch + src + G);
     s_uin[c * W + k] = v;
     s_un[c * W + k] = v;
-  }
-}
-
-// ghost cells of a non-periodic end inside the window, re-imaged from the new stage values
-template <int FLUX>
-__device__ __forceinline__ void sb_reimage(int bc_lo, int bc_hi, long long n, long long x0, int wcells, double* s_uin,
-                                           int W) {
-  constexpr int M = FluxM<FLUX>::m;
-  const int tid = threadIdx.x;
-  if (tid < 2 * G * M) {
-    const bool hi = tid >= G * M;
-    const int r = hi ? tid - G * M : tid;
-    const int c = r / G, g = r - c * G;
-    const int bc = hi ? bc_hi : bc_lo;
-    if (bc != WT_BC_PERIODIC) {
-      const long long xg = hi ? n + g : -1 - g;
-      const long long xs = (bc == WT_BC_OUTFLOW) ? (hi ? n - 1 : 0) : (hi ? n - 1 - g : g);
-      const long long pg = xg - x0, ps = xs - x0;
-      if (pg >= 0 && pg < wcells && ps >= 0 && ps < wcells) {
-        const double v = s_uin[c * W + ps];
-        s_uin[c * W + pg] = (bc == WT_BC_REFLECTIVE && c == 1) ? -v : v;
-      }
-    }
   }
 }
 
@@ -738,7 +811,7 @@ __global__ void __launch_bounds__(Tile1D<T + 4 * G, FluxM<FLUX>::m>::NT) stepblo
   for (long long step = 0;; ++step) {
     if (step > 0) {
       if (step >= p.n_steps) break;
-      // the previous step's last stage: stores of u^n, stop votes, alphas of u^n
+      // the previous step's last stage: stores of u^n (halos of this step) and stop votes
       if (!grid_wait(gbar, nbar * nblk)) {
         if (tid == 0) flag_error(ctl, WT_ERR_TIMEOUT);
         return;
@@ -754,40 +827,30 @@ __global__ void __launch_bounds__(Tile1D<T + 4 * G, FluxM<FLUX>::m>::NT) stepblo
     }
     __syncthreads();
 
-    double alpha[M], dt;
+    double alpha[M], dt = 0.0;
     long long lo;
     int Ts, off;
-    // ---- RK1 (alphas of u^n in slot 0)
-#pragma unroll
-    for (int f = 0; f < M; ++f) alpha[f] = bits_to_double(__ldcg(&ctl->amax[0][f]));
-    {
-      const double smax = (FLUX == WT_FLUX_EULER1D) ? ((alpha[0] < alpha[M - 1]) ? alpha[M - 1] : alpha[0]) : alpha[0];
-      dt = dt_fixed > 0.0 ? dt_fixed : MATH::cfl_dt(cfl, p.a[0].dx, smax);
-      const double rem = t_final - t;
-      if (rem < dt) dt = rem;
-    }
-    if (first && tid < 8) ctl->amax[2][tid] = 0ull;
-    if (first && tid == 0) ctl->dt = dt;
+    // ---- RK1: alphas of u^n (slot 0) from every CTA's phase B, then dt
     range(2 * G, lo, Ts, off);
-    stage1d_compute<MATH, FLUX, STAGE_RK1, TB, kStepBlocked>(p.a[0], lo, Ts, off, j0, j0 + Tc, alpha, dt, sm,
-                                                             AlphaWait{0ull, 0, -1});
-    sb_reimage<FLUX>(bc_lo, bc_hi, n, x0, wcells, s_uin, W);
-    grid_arrive(gbar);
-    ++nbar;
-    // ---- RK2 (alphas of u1 in slot 1, awaited after the alpha-free work)
-    range(G, lo, Ts, off);
-    if (!stage1d_compute<MATH, FLUX, STAGE_RK2, TB, kStepBlocked>(p.a[1], lo, Ts, off, j0, j0 + Tc, alpha, dt, sm,
-                                                                  AlphaWait{nbar * nblk, 1, first ? 0 : -1})) {
+    if (!stage1d_compute<MATH, FLUX, STAGE_RK1, TB, kStepBlocked>(
+            p.a[0], lo, Ts, off, j0, j0 + Tc, alpha, dt, sm,
+            AlphaWait{(++nbar) * nblk, 0, first ? 2 : -1, 1, cfl, dt_fixed, t, t_final})) {
       if (tid == 0) flag_error(ctl, WT_ERR_TIMEOUT);
       return;
     }
-    sb_reimage<FLUX>(bc_lo, bc_hi, n, x0, wcells, s_uin, W);
-    grid_arrive(gbar);
-    ++nbar;
-    // ---- RK3 (alphas of u2 in slot 2)
+    // ---- RK2: alphas of u1 (slot 1)
+    range(G, lo, Ts, off);
+    if (!stage1d_compute<MATH, FLUX, STAGE_RK2, TB, kStepBlocked>(
+            p.a[1], lo, Ts, off, j0, j0 + Tc, alpha, dt, sm,
+            AlphaWait{(++nbar) * nblk, 1, first ? 0 : -1, 0, 0.0, 0.0, 0.0, 0.0})) {
+      if (tid == 0) flag_error(ctl, WT_ERR_TIMEOUT);
+      return;
+    }
+    // ---- RK3: alphas of u2 (slot 2); u^{n+1} of the CTA's cells to global memory
     range(0, lo, Ts, off);
-    if (!stage1d_compute<MATH, FLUX, STAGE_RK3, TB, kStepBlocked>(p.a[2], lo, Ts, off, j0, j0 + Tc, alpha, dt, sm,
-                                                                  AlphaWait{nbar * nblk, 2, first ? 1 : -1})) {
+    if (!stage1d_compute<MATH, FLUX, STAGE_RK3, TB, kStepBlocked>(
+            p.a[2], lo, Ts, off, j0, j0 + Tc, alpha, dt, sm,
+            AlphaWait{(++nbar) * nblk, 2, first ? 1 : -1, 0, 0.0, 0.0, 0.0, 0.0})) {
       if (tid == 0) flag_error(ctl, WT_ERR_TIMEOUT);
       return;
     }

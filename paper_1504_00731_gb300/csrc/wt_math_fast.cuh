@@ -30,9 +30,12 @@ struct FastMath {
   __device__ __forceinline__ static double flux_advection(double a, double u) { return a * u; }
   __device__ __forceinline__ static double flux_burgers(double u) { return 0.5 * u * u; }
 
-  __device__ __forceinline__ static void euler_cell(const double* U, double gamma, double* f, double& u, double& H,
-                                                    double& sr, double& p) {
-    const double ir = 1.0 / U[0];
+  // 1 / rho and sqrt(rho) from one reciprocal square root
+  __device__ __forceinline__ static void euler_cell_ir(const double* U, double gamma, double* f, double& u, double& H,
+                                                       double& sr, double& p, double& ir) {
+    const double r = rsqrt(U[0]);
+    ir = r * r;
+    sr = U[0] * r;
     u = U[1] * ir;
     p = (gamma - 1.0) * fma(-0.5 * U[1], u, U[2]);
     const double e = U[2] + p;
@@ -40,13 +43,26 @@ struct FastMath {
     f[1] = fma(U[1], u, p);
     f[2] = e * u;
     H = e * ir;
-    sr = sqrt(U[0]);
+  }
+  __device__ __forceinline__ static void euler_cell(const double* U, double gamma, double* f, double& u, double& H,
+                                                    double& sr, double& p) {
+    double ir;
+    euler_cell_ir(U, gamma, f, u, H, sr, p, ir);
+  }
+  __device__ __forceinline__ static void euler_cell_speeds(const double* U, double gamma, double* f, double& u,
+                                                           double& H, double& sr, double* lam) {
+    double p, ir;
+    euler_cell_ir(U, gamma, f, u, H, sr, p, ir);
+    const double c = sqrt(gamma * p * ir);
+    lam[0] = fabs(u - c);
+    lam[1] = fabs(u);
+    lam[2] = fabs(u + c);
   }
 
+  // the wave speeds exactly as euler_cell_speeds computes them
   __device__ __forceinline__ static double euler_speeds(const double* U, double gamma, double* lam) {
-    const double ir = 1.0 / U[0];
-    const double u = U[1] * ir;
-    const double p = (gamma - 1.0) * fma(-0.5 * U[1], u, U[2]);
+    double f[3], u, H, sr, p, ir;
+    euler_cell_ir(U, gamma, f, u, H, sr, p, ir);
     const double c = sqrt(gamma * p * ir);
     lam[0] = fabs(u - c);
     lam[1] = fabs(u);

@@ -38,6 +38,17 @@ struct StrictMath {
     sr = sqrt(U[0]);
   }
 
+  // euler_cell and the wave speeds of euler_speeds from the same u and p
+  __device__ __forceinline__ static void euler_cell_speeds(const double* U, double gamma, double* f, double& u,
+                                                           double& H, double& sr, double* lam) {
+    double p;
+    euler_cell(U, gamma, f, u, H, sr, p);
+    const double c = sqrt(gamma * p / U[0]);
+    lam[0] = fabs(u - c);
+    lam[1] = fabs(u);
+    lam[2] = fabs(u + c);
+  }
+
   // |lambda_s| at a cell: (|u - c|, |u|, |u + c|), c = sqrt(gamma p / rho); returns p
   __device__ __forceinline__ static double euler_speeds(const double* U, double gamma, double* lam) {
     double u = U[1] / U[0];
