@@ -191,6 +191,7 @@ __device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long
   if (tid == 0) *reinterpret_cast<int*>(sm + TL::kQn) = 0;
   if (MODE == kStepBlocked && (tid >> 5) == kSW) {
     const int lane = tid & 31;
+    named_barrier_arrive(1, NT);  // phase B does not wait for the speeds
     unsigned long long vb[M];
 #pragma unroll
     for (int f = 0; f < M; ++f) vb[f] = 0ull;
@@ -211,7 +212,6 @@ __device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long
     }
 #pragma unroll
     for (int f = 0; f < M; ++f) vb[f] = warp_max_key(vb[f]);
-    named_barrier_arrive(1, NT);
     if (lane == 0) {
 #pragma unroll
       for (int f = 0; f < M; ++f) atomicMax(&ctl->amax[STAGE][f], vb[f]);
@@ -277,8 +277,22 @@ __device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long
   // step-blocked scalar fluxes have no phase C0: the alphas are awaited here
   if (MODE == kStepBlocked && FLUX != WT_FLUX_EULER1D) __syncthreads();
 
-  // ---- C0: Roe average and left eigenvectors per interface (interface i: cells i+2 | i+3)
-  if (FLUX == WT_FLUX_EULER1D) {
+  // ---- C0: Roe average and left eigenvectors per interface (interface i: cells i+2 | i+3);
+  // with MATH::kRoeRows one row of the matrix per thread
+  if (FLUX == WT_FLUX_EULER1D && MATH::kRoeRows) {
+    if (tid < 3 * ni) {
+      const int row = tid / ni, i = tid - row * ni;
+      double l[3], rs[3];
+      MATH::roe_row(s_sr[i + 2], s_vel[i + 2], s_H[i + 2], s_sr[i + 3], s_vel[i + 3], s_H[i + 3], a.gamma, row, l, rs);
+#pragma unroll
+      for (int e = 0; e < 3; ++e) s_L[(3 * row + e) * NI + i] = l[e];
+      if (row == 0) {
+#pragma unroll
+        for (int e = 0; e < 3; ++e) s_rs[e * NI + i] = rs[e];
+      }
+    }
+    __syncthreads();
+  } else if (FLUX == WT_FLUX_EULER1D) {
     for (int i = tid; i < ni; i += NT) {
       double L[9], rs[3];
       MATH::roe(s_sr[i + 2], s_vel[i + 2], s_H[i + 2], s_sr[i + 3], s_vel[i + 3], s_H[i + 3], a.gamma, L, rs);
@@ -400,7 +414,41 @@ __device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long
     hsrc = s_h;
   }
 
-  // ---- E: flux difference, RK combine, ghost images, wave speeds
+  // ---- E: flux difference, RK combine, ghost images, wave speeds.  Step-blocked: one
+  // (cell, component) per thread, and no wave speeds (phase B of the next stage takes them).
+  if (MODE == kStepBlocked && STAGE != STAGE_RHS) {
+    for (int idx = tid; idx < M * Tc; idx += NT) {
+      const int c = idx / Tc, t = idx - c * Tc;
+      const long long j = js + t;
+      const double hp = (FLUX == WT_FLUX_EULER1D) ? hsrc[c * NI + t + 1] : hsrc[t + 1] + hsrc[NI + t + 1];
+      const double hm = (FLUX == WT_FLUX_EULER1D) ? hsrc[c * NI + t] : hsrc[t] + hsrc[NI + t];
+      const double L = MATH::flux_diff(hp, hm, a.dx, a.inv_dx);
+      const double us = s_uin[c * W + off + t + G];
+      const double un = kNeedUn ? s_un[c * W + off + t + G] : us;
+      const double v = MATH::template rk<(STAGE == STAGE_RHS ? 0 : STAGE)>(un, us, dt, L);
+      s_uin[c * W + off + t + G] = v;
+      if (STAGE == STAGE_RK3) {
+        s_un[c * W + off + t + G] = v;
+        if (j >= own_lo && j < own_hi) {
+          if (!isfinite(v)) flag_error(ctl, WT_ERR_NONPHYSICAL);
+          double* o = a.uout + c * a.pitch;
+          o[j + G] = v;
+          // ghost images of this cell in the output
+          if (j < G || j >= n - G) {
+            const double vr = (c == 1) ? -v : v;
+            if (a.bc_hi == WT_BC_PERIODIC && j < G) o[n + j + G] = v;
+            if (a.bc_lo == WT_BC_PERIODIC && j >= n - G) o[j - n + G] = v;
+            if (a.bc_lo == WT_BC_OUTFLOW && j == 0) o[0] = o[1] = o[2] = v;
+            if (a.bc_hi == WT_BC_OUTFLOW && j == n - 1) o[n + 3] = o[n + 4] = o[n + 5] = v;
+            if (a.bc_lo == WT_BC_REFLECTIVE && j < G) o[2 - j] = vr;
+            if (a.bc_hi == WT_BC_REFLECTIVE && j >= n - G) o[2 * n + 2 - j] = vr;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    return true;
+  }
   unsigned long long vmax[M];
 #pragma unroll
   for (int f = 0; f < M; ++f) vmax[f] = 0ull;

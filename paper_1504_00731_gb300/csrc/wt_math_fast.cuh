@@ -7,7 +7,7 @@
 //   - comparisons of non-negative doubles on their bit patterns (integer pipe);
 //   - the weights of Eq. (om) over a common denominator prod_l (eps + beta_l), so one
 //     division per reconstruction; a restricted stencil (all beta = 0, Eq. (be_res)) has
-//     weights equal to gamma^theta and takes the linear combination directly;
+//     weights equal to gamma^theta and takes the equivalent linear scheme in closed form;
 //   - the restriction test R(beta) <= alpha_R as max beta <= alpha_R (eps + min beta);
 //   - the 1/2 of the flux splitting folded into the left eigenvectors.
 // Results agree with the strict policy to rounding.
@@ -19,6 +19,7 @@ namespace wt {
 
 struct FastMath {
   static constexpr bool kStrict = false;
+  static constexpr bool kRoeRows = false;  // Roe matrix one row per thread (roe_row)
   // projection v = kProj (L f +- alpha L u) with the stored L = kLScale * L_true
   static constexpr double kProj = 1.0, kLScale = 0.5;
 
@@ -99,6 +100,34 @@ struct FastMath {
     rs[2] = c;
   }
 
+  // Roe's mean state and row `row` of the (1/2-scaled) left eigenvectors, the rows written as
+  // one formula with row-dependent coefficients (no divergence between rows); rs as in roe
+  __device__ __forceinline__ static void roe_row(double sa, double ua, double Ha, double sb, double ub, double Hb,
+                                                 double gamma, int row, double* l, double* rs) {
+    const double is = 1.0 / (sa + sb);
+    const double wa = sa * is, wb = sb * is;
+    const double u = fma(wa, ua, wb * ub);
+    const double H = fma(wa, Ha, wb * Hb);
+    const double gm1 = gamma - 1.0;
+    const double c2 = gm1 * fma(-0.5 * u, u, H);
+    const double ic = rsqrt(c2);
+    const double hb1 = 0.5 * gm1 * ic * ic;
+    const double hb2 = 0.5 * u * u * hb1;
+    const double uic = 0.5 * u * ic;
+    const double hb1u = hb1 * u;
+    // rows: (0.5 (hb2 + uic), -0.5 hb1u - 0.25 ic, 0.5 hb1), (0.5 - hb2, hb1u, -hb1),
+    //       (0.5 (hb2 - uic), -0.5 hb1u + 0.25 ic, 0.5 hb1)
+    const double A = row == 1 ? -1.0 : 0.5, B = row == 0 ? 0.5 : (row == 1 ? 0.0 : -0.5);
+    const double C = row == 1 ? 0.5 : 0.0, D = row == 1 ? 1.0 : -0.5;
+    const double E = row == 0 ? -0.25 : (row == 1 ? 0.0 : 0.25), F = row == 1 ? -1.0 : 0.5;
+    l[0] = fma(A, hb2, fma(B, uic, C));
+    l[1] = fma(D, hb1u, E * ic);
+    l[2] = F * hb1;
+    rs[0] = u;
+    rs[1] = H;
+    rs[2] = c2 * ic;
+  }
+
   __device__ __forceinline__ static void project3(const double* l, const double* f, const double* U, double alpha,
                                                   double& vp, double& vm) {
     const double a = fma(l[2], f[2], fma(l[1], f[1], l[0] * f[0]));
@@ -166,11 +195,6 @@ struct FastMath {
     const double t6b = (s0 + s3) - (s1 + s2);        // q0 - 3 q1 + 2 q2 + 2 q3 - 3 q4 + q5
     const double tau5 = fma(C1312 * t5a, t5a, t5b * t5b);
     const double tau6 = fma(C1312 * t6a, t6a, 0.25 * (t6b * t6b));
-    // Eqs. (fh0)-(fh3) in difference form
-    w.fh[0] = fma(5.0 / 6.0, d1, fma(-1.0 / 3.0, d0, q[2]));
-    w.fh[1] = fma(1.0 / 6.0, d1, fma(1.0 / 3.0, d2, q[2]));
-    w.fh[2] = fma(2.0 / 3.0, d2, fma(-1.0 / 6.0, d3, q[2]));
-    w.fh[3] = fma(1.0 / 3.0, d4, fma(-5.0 / 6.0, d3, q[3]));
     // Eq. (tau_we6)
     w.theta1 = !(bits(tau6) < bits(tau5));
     w.tau = w.theta1 ? tau5 : tau6;
@@ -178,11 +202,22 @@ struct FastMath {
     const double bmax = nmax(nmax(b0, b1), nmax(b2, b3));
     const double bmin = nmin(nmin(b0, b1), nmin(b2, b3));
     if (!(bits(fma(alpha_R, bmin, alpha_R * eps)) < bits(bmax))) {
-      double c0, c1, c2, c3;  // Eq. (gam_we6)
-      gammas(w.theta1, c0, c1, c2, c3);
-      out = fma(c3, w.fh[3], fma(c2, w.fh[2], fma(c1, w.fh[1], c0 * w.fh[0])));
+      // restricted: the weights are gamma^theta (Eq. (gam_we6)) and sum_k gamma_k fh_k is the
+      // linear scheme q2 + sum_j c_j (q_{j+1} - q_j) / 60; theta = 1: (-2, 11, 24, -3, 0),
+      // theta = 0: (-1, 7, 30, -7, 1)
+      const double c0 = w.theta1 ? -2.0 / 60.0 : -1.0 / 60.0;
+      const double c1 = w.theta1 ? 11.0 / 60.0 : 7.0 / 60.0;
+      const double c2 = w.theta1 ? 24.0 / 60.0 : 30.0 / 60.0;
+      const double c3 = w.theta1 ? -3.0 / 60.0 : -7.0 / 60.0;
+      const double c4 = w.theta1 ? 0.0 : 1.0 / 60.0;
+      out = fma(c4, d4, fma(c3, d3, fma(c2, d2, fma(c1, d1, c0 * d0)))) + q[2];
       return true;
     }
+    // Eqs. (fh0)-(fh3) in difference form
+    w.fh[0] = fma(5.0 / 6.0, d1, fma(-1.0 / 3.0, d0, q[2]));
+    w.fh[1] = fma(1.0 / 6.0, d1, fma(1.0 / 3.0, d2, q[2]));
+    w.fh[2] = fma(2.0 / 3.0, d2, fma(-1.0 / 6.0, d3, q[2]));
+    w.fh[3] = fma(1.0 / 3.0, d4, fma(-5.0 / 6.0, d3, q[3]));
     w.e[0] = eps + b0;
     w.e[1] = eps + b1;
     w.e[2] = eps + b2;

@@ -10,6 +10,7 @@ namespace wt {
 
 struct StrictMath {
   static constexpr bool kStrict = true;
+  static constexpr bool kRoeRows = false;  // the whole Roe matrix per interface (roe)
   // projection v = kProj (L f +- alpha L u) with the stored L = kLScale * L_true
   static constexpr double kProj = 0.5, kLScale = 1.0;
   // the reconstruction is evaluated in one piece (weno_flags)
@@ -82,6 +83,9 @@ struct StrictMath {
     rs[1] = H;
     rs[2] = c;
   }
+
+  __device__ __forceinline__ static void roe_row(double, double, double, double, double, double, double, int,
+                                                 double*, double*) {}
 
   // ---- Global Lax-Friedrichs splitting of one projected cell (Eq. (flux_split_lf))
   __device__ __forceinline__ static void project3(const double* l, const double* f, const double* U, double alpha,
