@@ -40,11 +40,13 @@ class Problem(ctypes.Structure):
         ("alpha_R", ctypes.c_double),
         ("bc_lo", ctypes.c_int32 * 2),
         ("bc_hi", ctypes.c_int32 * 2),
+        ("gravity", ctypes.c_double),
     ]
 
 
-def problem(flux, gamma=1.4, adv_speed=1.0, eps=1e-10, alpha_R=50.0, bc=BC_PERIODIC, bc_y=None):
-    """Build a Problem; ``bc`` is one code or a (lo, hi) pair, ``bc_y`` likewise for 2D."""
+def problem(flux, gamma=1.4, adv_speed=1.0, eps=1e-10, alpha_R=50.0, bc=BC_PERIODIC, bc_y=None, gravity=0.0):
+    """Build a Problem; ``bc`` is one code or a (lo, hi) pair, ``bc_y`` likewise for 2D; ``gravity``
+    is g of the 2D source terms (TEST 6, Sec. 4.3), 0 for none."""
     p = Problem()
     p.flux = flux
     p.m = _M[flux]
@@ -57,6 +59,7 @@ def problem(flux, gamma=1.4, adv_speed=1.0, eps=1e-10, alpha_R=50.0, bc=BC_PERIO
     ylo, yhi = (by, by) if isinstance(by, int) else by
     p.bc_lo[0], p.bc_hi[0] = lo, hi
     p.bc_lo[1], p.bc_hi[1] = ylo, yhi
+    p.gravity = gravity
     return p
 
 

@@ -112,6 +112,7 @@ struct Problem {
   double eps;        /* epsilon of Eq. (om) and of R(beta) in Eq. (be_res) */
   double alpha_R;    /* threshold of Eq. (be_res) */
   int32_t bc_lo[2], bc_hi[2]; /* per direction x, y */
+  double gravity;    /* 2D Euler: g of the source terms -g rho (y momentum) and -g rho v (energy), TEST 6 of Sec. 4.3 */
 };
 
 const int G = 3; /* ghost cells per side: the six-point stencil S^6 = {j-2..j+3} (Sec. 2, Remark on flux splitting) */
@@ -566,6 +567,14 @@ void rhs(const Problem& P, const Grid& g, const R* u, R* Lout, long long* theta1
         Lout[idx] = Lout[idx] + (-(hp - hm) / g.dy);
       }
   }
+  /* gravity in -y (TEST 6, Sec. 4.3): -g rho added to the y-momentum and -g rho v to the energy
+   * equation, rho v being the conserved y momentum */
+  if (P.gravity != 0.0) {
+    for (int64_t j = 0; j < cells; ++j) {
+      Lout[2 * cells + j] = Lout[2 * cells + j] + (-(P.gravity * u[j]));
+      Lout[3 * cells + j] = Lout[3 * cells + j] + (-(P.gravity * u[2 * cells + j]));
+    }
+  }
 }
 
 /* ------------------------------------------------------------------------- */
@@ -783,6 +792,10 @@ void wto_rhs_at(const Problem* P, int64_t nx, int64_t ny, double dx, double dy, 
     for (int c = 0; c < m; ++c) {
       double hp = hF[(size_t)c * (ny + 1) + (y + 1)], hm = hF[(size_t)c * (ny + 1) + y];
       out[q * m + c] = out[q * m + c] + (-(hp - hm) / dy);
+    }
+    if (P->gravity != 0.0) {
+      out[q * m + 2] = out[q * m + 2] + (-(P->gravity * u[cells[q]]));
+      out[q * m + 3] = out[q * m + 3] + (-(P->gravity * u[2 * all + cells[q]]));
     }
   }
 }

@@ -252,3 +252,45 @@ def euler2d_vortices(nx: int, ny: int, seed: int, n_vortex=8, rc=0.05, gamma=GAM
     u = q_u[quad] + du
     v = q_v[quad] + dv
     return cons_2d(rho, u, v, p, gamma), dx, dy
+
+
+# --------------------------------------------------------------------------------------------
+# Test problems of Sec. 4.2 / 4.3 that run on the existing kernels (reflective walls, gravity)
+# --------------------------------------------------------------------------------------------
+def blast_waves(n: int):
+    """Two interacting blast waves, Eq. (blast_prob) (TEST 5): (rho, u, p) = (1, 0, 1000) on
+    (0, 0.1), (1, 0, 0.01) on (0.1, 0.9), (1, 0, 100) on (0.9, 1); reflective walls at both
+    ends; the paper takes alpha_R = 10 and t = 0.038 on N = 801."""
+    x, dx = grid_1d(n, 0.0, 1.0, periodic=False)
+    p = np.where(x < 0.1, 1000.0, np.where(x < 0.9, 0.01, 100.0))
+    return cons_1d(np.ones(n), np.zeros(n), p), x, dx
+
+
+RT_GRAVITY = 0.1
+
+
+def rayleigh_taylor(nx: int, ny: int, g=RT_GRAVITY, gamma=GAMMA):
+    """Rayleigh-Taylor instability (TEST 6, Sec. 4.3) on (-0.25, 0.25) x (-0.75, 0.75): rho = 2
+    for y >= 0 and 1 below, hydrostatic p = 2.5 - rho g y, u = 0,
+    v = (0.01 / 4)(1 + cos 4 pi x)(1 + cos(4 pi y / 3)); periodic in x, reflective in y, source
+    terms with g = 0.1.  Cell centres, so the data are mirror-symmetric about x = 0."""
+    x, dx = grid_1d(nx, -0.25, 0.25, periodic=False)
+    x = 0.5 * (x - x[::-1])  # exactly antisymmetric cell centres
+    y, dy = grid_1d(ny, -0.75, 0.75, periodic=False)
+    X, Y = np.meshgrid(x, y)
+    rho = np.where(Y >= 0.0, 2.0, 1.0)
+    p = 2.5 - rho * g * Y
+    v = 0.0025 * (1.0 + np.cos(4.0 * np.pi * X)) * (1.0 + np.cos(4.0 * np.pi * Y / 3.0))
+    return cons_2d(rho, np.zeros_like(X), v, p, gamma), dx, dy
+
+
+def implosion(n: int, gamma=GAMMA):
+    """Implosion problem, Eq. (eu2D_im) (TEST 7) on (0, 1)^2: (rho, p) = (1, 1) for
+    x + y > 1/2 and (0.125, 0.14) otherwise, at rest, reflective walls; the paper takes
+    alpha_R = 1 and t = 5 on 400 x 400.  Symmetric about the diagonal x = y."""
+    x, dx = grid_1d(n, 0.0, 1.0, periodic=False)
+    X, Y = np.meshgrid(x, x)
+    inner = X + Y > 0.5
+    rho = np.where(inner, 1.0, 0.125)
+    p = np.where(inner, 1.0, 0.14)
+    return cons_2d(rho, np.zeros_like(X), np.zeros_like(X), p, gamma), dx, dx
