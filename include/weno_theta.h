@@ -81,6 +81,10 @@ typedef struct {
   int32_t bc_hi[2];   /* wt_bc at x = hi */
   int32_t mode;       /* wt_mode */
   int32_t reserved;   /* must be 0 */
+  double gravity;     /* 2D Euler only: g of the source terms -g rho (y momentum) and -g rho v
+                         (energy) of the Rayleigh-Taylor test (TEST 6, Sec. 4.3), gravity along
+                         -y; 0 for none.  Must be finite; nonzero for another flux is
+                         WT_ERR_UNSUPPORTED. */
 } wt_problem;
 
 typedef struct {

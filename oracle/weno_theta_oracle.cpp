@@ -443,12 +443,19 @@ void line_fluxes(const Problem& P, Line<R>& L, int dir, const R* alpha, std::vec
       R vp[6], vm[6], qp[6], qm[6];
       for (int k = 0; k < 6; ++k) {
         int cell = i - 2 + k;
+        /* l_s . f and l_s . u, summed density, normal momentum, tangential momentum (2D),
+         * energy: the same order in both sweep directions */
         R a = Lm[s][0] * F.at(0, cell);
         R b = Lm[s][0] * L.at(0, cell);
-        for (int c = 1; c < m; ++c) {
-          a = a + Lm[s][c] * F.at(c, cell);
-          b = b + Lm[s][c] * L.at(c, cell);
+        const int nc = (m == 4) ? 1 + dir : 1, tc = 2 - dir;
+        a = a + Lm[s][nc] * F.at(nc, cell);
+        b = b + Lm[s][nc] * L.at(nc, cell);
+        if (m == 4) {
+          a = a + Lm[s][tc] * F.at(tc, cell);
+          b = b + Lm[s][tc] * L.at(tc, cell);
         }
+        a = a + Lm[s][m - 1] * F.at(m - 1, cell);
+        b = b + Lm[s][m - 1] * L.at(m - 1, cell);
         vp[k] = 0.5 * (a + alpha[s] * b);
         vm[k] = 0.5 * (a - alpha[s] * b);
       }
@@ -463,9 +470,12 @@ void line_fluxes(const Problem& P, Line<R>& L, int dir, const R* alpha, std::vec
       if (theta1_count) *theta1_count += ip.theta + im.theta;
       if (restricted_count) *restricted_count += ip.restricted + im.restricted;
     }
+    /* h = R (F+ + F-): the two acoustic fields (u - c, u + c) summed first, then the others,
+     * so that a mirrored state gives the mirrored flux in floating point too */
     for (int c = 0; c < m; ++c) {
-      R h = Rm[c][0] * Fs[0];
-      for (int s = 1; s < m; ++s) h = h + Rm[c][s] * Fs[s];
+      R h = Rm[c][0] * Fs[0] + Rm[c][m - 1] * Fs[m - 1];
+      if (m == 3) h = h + Rm[c][1] * Fs[1];
+      else h = h + (Rm[c][1] * Fs[1] + Rm[c][2] * Fs[2]);
       hF[(size_t)c * (n + 1) + (i + 1)] = h;
     }
   }

@@ -46,6 +46,7 @@ class WtProblem(ctypes.Structure):
         ("bc_hi", ctypes.c_int32 * 2),
         ("mode", ctypes.c_int32),
         ("reserved", ctypes.c_int32),
+        ("gravity", ctypes.c_double),
     ]
 
 
@@ -123,7 +124,7 @@ def _check(status):
 
 
 def problem(flux, gamma=1.4, adv_speed=1.0, eps=1e-10, alpha_R=50.0, bc=WT_BC_PERIODIC, bc_y=None,
-            mode=WT_MODE_FAST) -> WtProblem:
+            mode=WT_MODE_FAST, gravity=0.0) -> WtProblem:
     p = WtProblem()
     p.flux = flux
     p.m = _M[flux]
@@ -137,6 +138,7 @@ def problem(flux, gamma=1.4, adv_speed=1.0, eps=1e-10, alpha_R=50.0, bc=WT_BC_PE
     p.bc_lo[0], p.bc_hi[0], p.bc_lo[1], p.bc_hi[1] = lo, hi, ylo, yhi
     p.mode = mode
     p.reserved = 0
+    p.gravity = gravity
     return p
 
 

@@ -66,6 +66,9 @@ int check_problem(const wt_problem* p) {
     return fail(WT_ERR_UNSUPPORTED, "reflective boundaries are defined for the Euler equations only");
   if ((p->bc_lo[0] == WT_BC_PERIODIC) != (p->bc_hi[0] == WT_BC_PERIODIC))
     return fail(WT_ERR_ARG, "a periodic boundary must be periodic at both ends");
+  if (!std::isfinite(p->gravity)) return fail(WT_ERR_ARG, "gravity not finite");
+  if (p->gravity != 0.0 && p->flux != WT_FLUX_EULER2D)
+    return fail(WT_ERR_UNSUPPORTED, "gravity source terms are defined for the 2D Euler equations only");
   return WT_OK;
 }
 
@@ -464,6 +467,7 @@ Stage2DArgs base_args_2d(const wt_problem* p, const wt_grid* g, const Layout2D& 
   a.gamma = p->gamma;
   a.eps = p->eps;
   a.alpha_R = p->alpha_R;
+  a.gravity = p->gravity;
   a.bcx_lo = p->bc_lo[0];
   a.bcx_hi = p->bc_hi[0];
   a.bcy_lo = p->bc_lo[1];

@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(Tile2D<TX, TY>::NT) stage2d_kernel(const Stage
       const int k = (r + G) * WX + i + kk;
       const double f[4] = {s_fx[k], s_fx[NCELL + k], s_fx[2 * NCELL + k], s_fx[3 * NCELL + k]};
       const double U[4] = {s_uin[k], s_uin[NCELL + k], s_uin[2 * NCELL + k], s_uin[3 * NCELL + k]};
-      MATH::project4(l, f, U, al, vp[kk], vm[kk]);
+      MATH::project4(0, l, f, U, al, vp[kk], vm[kk]);
     }
     double qm[6];
 #pragma unroll
@@ -266,7 +266,7 @@ __global__ void __launch_bounds__(Tile2D<TX, TY>::NT) stage2d_kernel(const Stage
       const int k = (j + kk) * WX + t + G;
       const double f[4] = {s_fy[k], s_fy[NCELL + k], s_fy[2 * NCELL + k], s_fy[3 * NCELL + k]};
       const double U[4] = {s_uin[k], s_uin[NCELL + k], s_uin[2 * NCELL + k], s_uin[3 * NCELL + k]};
-      MATH::project4(l, f, U, al, vp[kk], vm[kk]);
+      MATH::project4(1, l, f, U, al, vp[kk], vm[kk]);
     }
     double qm[6];
 #pragma unroll
@@ -296,7 +296,9 @@ __global__ void __launch_bounds__(Tile2D<TX, TY>::NT) stage2d_kernel(const Stage
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       const double Ly = MATH::flux_diff(s_h[c * NI + (r + 1) * tcx + t], s_h[c * NI + r * tcx + t], a.dy, a.inv_dy);
-      const double L = MATH::add_sweeps(s_Lx[c * TX * TY + r * TX + t], Ly);
+      double L = MATH::add_sweeps(s_Lx[c * TX * TY + r * TX + t], Ly);
+      // gravity along -y (TEST 6, Sec. 4.3): -g rho on the y momentum, -g rho v on the energy
+      if (c >= 2 && a.gravity != 0.0) L = MATH::add_source(L, a.gravity, s_uin[(c == 2 ? 0 : 2) * NCELL + kc]);
       if (STAGE == STAGE_RHS) {
         a.Lout[(c * ny + y) * nx + x] = L;
       } else {

@@ -79,6 +79,7 @@ struct Stage2DArgs {
   long long planep;      // padded plane stride
   double dx, dy, inv_dx, inv_dy;
   double gamma, eps, alpha_R;
+  double gravity;        // g of the source terms (0: none)
   int bcx_lo, bcx_hi, bcy_lo, bcy_hi;
   Ctl* ctl;
 };

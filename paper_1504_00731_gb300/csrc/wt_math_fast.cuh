@@ -24,6 +24,11 @@ struct FastMath {
   static constexpr double kProj = 1.0, kLScale = 0.5;
 
   __device__ __forceinline__ static long long bits(double x) { return __double_as_longlong(x); }
+  // a b + c d with both products rounded and no contraction into an FMA: the same value when
+  // the two terms trade places (mirrored or transposed data give mirrored or transposed fluxes)
+  __device__ __forceinline__ static double dot2(double a, double b, double c, double d) {
+    return __dadd_rn(__dmul_rn(a, b), __dmul_rn(c, d));
+  }
   // max / min / less-than of non-negative doubles through their bit patterns
   __device__ __forceinline__ static double nmax(double a, double b) { return bits(a) < bits(b) ? b : a; }
   __device__ __forceinline__ static double nmin(double a, double b) { return bits(b) < bits(a) ? b : a; }
@@ -76,8 +81,8 @@ struct FastMath {
                                              double gamma, double* L, double* rs) {
     const double is = 1.0 / (sa + sb);
     const double wa = sa * is, wb = sb * is;
-    const double u = fma(wa, ua, wb * ub);
-    const double H = fma(wa, Ha, wb * Hb);
+    const double u = dot2(wa, ua, wb, ub);
+    const double H = dot2(wa, Ha, wb, Hb);
     const double gm1 = gamma - 1.0;
     const double c2 = gm1 * fma(-0.5 * u, u, H);
     const double ic = rsqrt(c2);
@@ -106,8 +111,8 @@ struct FastMath {
                                                  double gamma, int row, double* l, double* rs) {
     const double is = 1.0 / (sa + sb);
     const double wa = sa * is, wb = sb * is;
-    const double u = fma(wa, ua, wb * ub);
-    const double H = fma(wa, Ha, wb * Hb);
+    const double u = dot2(wa, ua, wb, ub);
+    const double H = dot2(wa, Ha, wb, Hb);
     const double gm1 = gamma - 1.0;
     const double c2 = gm1 * fma(-0.5 * u, u, H);
     const double ic = rsqrt(c2);
@@ -260,8 +265,10 @@ struct FastMath {
     h[2] = fma(H, s02, fma(u * c, d20, 0.5 * u * u * F[1]));
   }
 
+  // rounded on its own (never contracted into the sum of the two sweeps), so that
+  // Lx + Ly is the same value for transposed data
   __device__ __forceinline__ static double flux_diff(double hp, double hm, double, double inv_dx) {
-    return (hm - hp) * inv_dx;
+    return __dmul_rn(hm - hp, inv_dx);
   }
 
   template <int S>
@@ -279,14 +286,14 @@ struct FastMath {
     const double ir = 1.0 / U[0];
     u = U[1] * ir;
     v = U[2] * ir;
-    const double p = (gamma - 1.0) * fma(-0.5 * U[1], u, fma(-0.5 * U[2], v, U[3]));
+    const double p = (gamma - 1.0) * fma(-0.5, dot2(U[1], u, U[2], v), U[3]);
     const double e = U[3] + p;
     f[0] = U[1];
     f[1] = fma(U[1], u, p);
     f[2] = U[1] * v;
     f[3] = e * u;
     g[0] = U[2];
-    g[1] = f[2];
+    g[1] = U[2] * u;  // rho v u, computed as the transpose of f[2]
     g[2] = fma(U[2], v, p);
     g[3] = e * v;
     H = e * ir;
@@ -297,7 +304,7 @@ struct FastMath {
                                                         double* lx, double* ly, double& q) {
     const double ir = 1.0 / U[0];
     const double u = U[1] * ir, v = U[2] * ir;
-    const double p = (gamma - 1.0) * fma(-0.5 * U[1], u, fma(-0.5 * U[2], v, U[3]));
+    const double p = (gamma - 1.0) * fma(-0.5, dot2(U[1], u, U[2], v), U[3]);
     const double c = sqrt(gamma * p * ir);
     const double au = fabs(u), av = fabs(v);
     lx[0] = fabs(u - c);
@@ -316,10 +323,10 @@ struct FastMath {
                                                double ub, double vb, double Hb, double gamma, double* L, double* rs) {
     const double is = 1.0 / (sa + sb);
     const double wa = sa * is, wb = sb * is;
-    const double u = fma(wa, ua, wb * ub);
-    const double v = fma(wa, va, wb * vb);
-    const double H = fma(wa, Ha, wb * Hb);
-    const double q2 = fma(u, u, v * v);
+    const double u = dot2(wa, ua, wb, ub);
+    const double v = dot2(wa, va, wb, vb);
+    const double H = dot2(wa, Ha, wb, Hb);
+    const double q2 = dot2(u, u, v, v);
     const double gm1 = gamma - 1.0;
     const double c2 = gm1 * fma(-0.5, q2, H);
     const double ic = rsqrt(c2);
@@ -348,10 +355,12 @@ struct FastMath {
     rs[3] = c;
   }
 
-  __device__ __forceinline__ static void project4(const double* l, const double* f, const double* U, double alpha,
-                                                  double& vp, double& vm) {
-    const double a = fma(l[3], f[3], fma(l[2], f[2], fma(l[1], f[1], l[0] * f[0])));
-    const double b = fma(l[3], U[3], fma(l[2], U[2], fma(l[1], U[1], l[0] * U[0])));
+  // density, normal momentum, tangential momentum, energy: the same order in both directions
+  __device__ __forceinline__ static void project4(int dir, const double* l, const double* f, const double* U,
+                                                  double alpha, double& vp, double& vm) {
+    const int n = 1 + dir, t = 2 - dir;
+    const double a = fma(l[3], f[3], fma(l[t], f[t], fma(l[n], f[n], l[0] * f[0])));
+    const double b = fma(l[3], U[3], fma(l[t], U[t], fma(l[n], U[n], l[0] * U[0])));
     vp = fma(alpha, b, a);
     vm = fma(-alpha, b, a);
   }
@@ -361,7 +370,7 @@ struct FastMath {
     const double s03 = F[0] + F[3], d30 = F[3] - F[0];
     const double a = s03 + F[1];
     h[0] = a;
-    const double hq2 = 0.5 * fma(u, u, v * v);
+    const double hq2 = 0.5 * dot2(u, u, v, v);
     if (dir == 0) {
       h[1] = fma(u, a, c * d30);
       h[2] = fma(v, a, F[2]);
@@ -374,6 +383,8 @@ struct FastMath {
   }
 
   __device__ __forceinline__ static double add_sweeps(double Lx, double Ly) { return Lx + Ly; }
+  // L + (-g q): a source term -g q added to the flux divergence
+  __device__ __forceinline__ static double add_source(double L, double g, double q) { return fma(-g, q, L); }
   __device__ __forceinline__ static double cfl_dt_2d(double cfl, double smax) { return cfl / smax; }
 };
 

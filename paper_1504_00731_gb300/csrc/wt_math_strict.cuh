@@ -197,9 +197,10 @@ struct StrictMath {
   // ---- back-projection h = R (F+ + F-) with R = [r_1 r_2 r_3] of Roe's matrix
   __device__ __forceinline__ static void backproject(const double* rs, const double* F, double* h) {
     const double u = rs[0], H = rs[1], c = rs[2];
-    h[0] = 1.0 * F[0] + 1.0 * F[1] + 1.0 * F[2];
-    h[1] = (u - c) * F[0] + u * F[1] + (u + c) * F[2];
-    h[2] = (H - u * c) * F[0] + 0.5 * u * u * F[1] + (H + u * c) * F[2];
+    // the acoustic pair (fields 0 and 2) first, so that mirrored data give mirrored fluxes
+    h[0] = (1.0 * F[0] + 1.0 * F[2]) + 1.0 * F[1];
+    h[1] = ((u - c) * F[0] + (u + c) * F[2]) + u * F[1];
+    h[2] = ((H - u * c) * F[0] + (H + u * c) * F[2]) + 0.5 * u * u * F[1];
   }
 
   // ---- Eq. (mod_semi)
@@ -283,14 +284,17 @@ struct StrictMath {
     rs[3] = c;
   }
 
-  __device__ __forceinline__ static void project4(const double* l, const double* f, const double* U, double alpha,
-                                                  double& vp, double& vm) {
+  // summed density, normal momentum, tangential momentum, energy: the same order in both
+  // sweep directions, so that transposed data give transposed fluxes
+  __device__ __forceinline__ static void project4(int dir, const double* l, const double* f, const double* U,
+                                                  double alpha, double& vp, double& vm) {
+    const int n = 1 + dir, t = 2 - dir;
     double a = l[0] * f[0];
     double b = l[0] * U[0];
-    a = a + l[1] * f[1];
-    b = b + l[1] * U[1];
-    a = a + l[2] * f[2];
-    b = b + l[2] * U[2];
+    a = a + l[n] * f[n];
+    b = b + l[n] * U[n];
+    a = a + l[t] * f[t];
+    b = b + l[t] * U[t];
     a = a + l[3] * f[3];
     b = b + l[3] * U[3];
     vp = 0.5 * (a + alpha * b);
@@ -313,16 +317,17 @@ struct StrictMath {
       R[8] = v - c;     R[9] = v;          R[10] = 0.0; R[11] = v + c;
       R[12] = H - v * c; R[13] = 0.5 * q2; R[14] = u;   R[15] = H + v * c;
     }
+    // the acoustic pair (fields 0 and 3) first, then entropy + shear: mirror-symmetric sums
     for (int r = 0; r < 4; ++r) {
-      double x = R[4 * r] * F[0];
-      x = x + R[4 * r + 1] * F[1];
-      x = x + R[4 * r + 2] * F[2];
-      x = x + R[4 * r + 3] * F[3];
+      double x = R[4 * r] * F[0] + R[4 * r + 3] * F[3];
+      x = x + (R[4 * r + 1] * F[1] + R[4 * r + 2] * F[2]);
       h[r] = x;
     }
   }
 
   __device__ __forceinline__ static double add_sweeps(double Lx, double Ly) { return Lx + Ly; }
+  // L + (-g q): a source term -g q added to the flux divergence
+  __device__ __forceinline__ static double add_source(double L, double g, double q) { return L + (-(g * q)); }
   __device__ __forceinline__ static double cfl_dt_2d(double cfl, double smax) { return cfl / smax; }
 };
 

@@ -426,28 +426,29 @@ def test_hydrostatic_balance_with_gravity(oracle):
 
 
 def test_rayleigh_taylor_and_implosion_keep_their_symmetry(oracle):
-    """The symmetry the paper reports for WENO-theta (TEST 6, TEST 7 of Sec. 4.3): Rayleigh-
-    Taylor data mirrored about x = 0 stay mirrored (rho u odd) under gravity with periodic x and
-    reflective y; implosion data symmetric about x = y stay symmetric (rho u and rho v
-    exchanged) with reflective walls and alpha_R = 1.  Exact arithmetic keeps both symmetries;
-    a literal binary64 evaluation breaks them only at round-off (the back-projection sums the
-    characteristic fields in a fixed order, which the mirror image reverses), so the bound is a
-    few ulp of the field, not bit equality."""
+    """The symmetry the paper reports for WENO-theta (TEST 6, TEST 7 of Sec. 4.3), bit for bit:
+    Rayleigh-Taylor data mirrored about x = 0 stay mirrored (rho u odd) under gravity with
+    periodic x and reflective y; implosion data symmetric about x = y stay symmetric (rho u and
+    rho v exchanged) with reflective walls and alpha_R = 1.  Exact arithmetic keeps both; in
+    binary64 they hold because the back-projection adds the two acoustic fields first and the
+    projections add the normal momentum before the tangential one in both sweeps (a reading:
+    the paper does not fix the order of these sums).  With the plain index order the mirror
+    image drifts from the first steps on, and the instabilities of both problems amplify that
+    round-off to order-one asymmetry by the paper's final times."""
     O = oracle
     U, dx, dy = W.rayleigh_taylor(16, 48)
     P = O.problem(O.FLUX_EULER2D, bc=O.BC_PERIODIC, bc_y=O.BC_REFLECTIVE, gravity=W.RT_GRAVITY)
-    r, t, s = O.run(P, U, dx, dy, cfl=0.5, n_steps=40)
-    assert s == 40 and not np.array_equal(r, U)
-    scale = np.abs(r).max()  # round-off of the characteristic sums is relative to the whole state
+    r, t, s = O.run(P, U, dx, dy, cfl=0.5, n_steps=300)
+    assert s == 300
     for c, sign in enumerate((1.0, -1.0, 1.0, 1.0)):
-        assert np.abs(r[c] - sign * r[c][:, ::-1]).max() <= 1e-14 * scale, c
-    assert np.abs(r[1]).max() > 1e-4  # the instability has started to move fluid sideways
+        assert np.array_equal(r[c], sign * r[c][:, ::-1]), c
+    assert np.abs(r[1]).max() > 1e-3  # the instability moves fluid sideways
     V, dx, dy = W.implosion(24)
     P = O.problem(O.FLUX_EULER2D, bc=O.BC_REFLECTIVE, bc_y=O.BC_REFLECTIVE, alpha_R=1.0)
-    r, t, s = O.run(P, V, dx, dy, cfl=0.5, n_steps=40)
-    scale = np.abs(r).max()
-    for a, b in ((r[0], r[0].T), (r[3], r[3].T), (r[1], r[2].T)):
-        assert np.abs(a - b).max() <= 1e-14 * scale
+    r, t, s = O.run(P, V, dx, dy, cfl=0.5, n_steps=300)
+    assert np.array_equal(r[0], r[0].T) and np.array_equal(r[3], r[3].T)
+    assert np.array_equal(r[1], r[2].T)
+    assert not np.array_equal(r, V)
 
 
 def test_blast_waves_against_exact_riemann_solutions(oracle):
