@@ -297,6 +297,49 @@ def adjoint_measure(B, dev, nprob=256, n=16384, steps=64, K=32):
             "workload": "256 x 1D Euler N=16384 (seeded Riemann + entropy wave), outflow, CFL 0.5"}
 
 
+def problems_measure(B, dev):
+    """The test problems of Sec. 4.2 / 4.3 built on reflective walls and gravity: two
+    interacting blast waves (TEST 5, N = 801, alpha_R = 10, the paper's run to t = 0.038), the
+    Rayleigh-Taylor instability (TEST 6, 120 x 360, gravity 0.1, 2000 of the ~17600 steps to
+    t = 9.5) and the implosion problem (TEST 7, 400 x 400, alpha_R = 1, 1000 of the ~16200
+    steps to t = 5); fast mode, CFL 0.5, cell-updates/s through weno_theta_step."""
+    import torch
+
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {}
+    cases = []
+    U, x, dx = W.blast_waves(801)
+    cases.append(("blast_waves_N801_t0.038", U, B.problem(B.WT_FLUX_EULER1D, bc=B.WT_BC_REFLECTIVE, mode=B.WT_MODE_FAST,
+                                                          alpha_R=10.0), B.grid_1d(801, 0.0, 1.0),
+                  dict(t_final=0.038)))
+    U, dx, dy = W.rayleigh_taylor(120, 360)
+    cases.append(("rayleigh_taylor_120x360_2000steps", U,
+                  B.problem(B.WT_FLUX_EULER2D, bc=B.WT_BC_PERIODIC, bc_y=B.WT_BC_REFLECTIVE, mode=B.WT_MODE_FAST,
+                            gravity=W.RT_GRAVITY), B.grid_2d(120, 360, (-0.25, -0.75), (0.25, 0.75)),
+                  dict(max_steps=2000)))
+    U, dx, dy = W.implosion(400)
+    cases.append(("implosion_400x400_1000steps", U,
+                  B.problem(B.WT_FLUX_EULER2D, bc=B.WT_BC_REFLECTIVE, bc_y=B.WT_BC_REFLECTIVE, mode=B.WT_MODE_FAST,
+                            alpha_R=1.0), B.grid_2d(400, 400), dict(max_steps=1000)))
+    for name, U, prob, grid, kw in cases:
+        ws = B.alloc_workspace(B.workspace_bytes(prob, grid), dev)
+        u0 = torch.from_numpy(np.ascontiguousarray(U)).to(dev)
+        u = u0.clone()
+        B.weno_theta_step(prob, grid, u, 0.5, ws, max_steps=3)
+        u.copy_(u0)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        t, steps = B.weno_theta_step(prob, grid, u, 0.5, ws, **kw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) * 1e-3
+        cells = int(np.prod(U.shape[1:]))
+        out[name] = {"value": cells * steps / sec, "unit": "cell-updates/s", "cells": cells, "rk_steps": steps,
+                     "t_reached": t, "seconds": sec, "finite": bool(torch.isfinite(u).all())}
+    return out
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -461,6 +504,7 @@ def run_ours(args):
             line["batched"] = batched_measure(B, dev)
             line["euler2d"] = euler2d_measure(B, dev)
             line["adjoint"] = adjoint_measure(B, dev)
+            line["problems"] = problems_measure(B, dev)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)
