@@ -294,3 +294,65 @@ def implosion(n: int, gamma=GAMMA):
     rho = np.where(inner, 1.0, 0.125)
     p = np.where(inner, 1.0, 0.14)
     return cons_2d(rho, np.zeros_like(X), np.zeros_like(X), p, gamma), dx, dx
+
+
+# --------------------------------------------------------------------------------------------
+# The remaining 1D validation set of Sec. 3.3 / 4.1 / 4.2
+# --------------------------------------------------------------------------------------------
+def sine_max(n: int):
+    """u0 = max(sin pi x, 0) on (-1, 1), periodic (Eq. (sca_ini_3), resolution test)."""
+    x, dx = grid_1d(n, -1.0, 1.0, periodic=True)
+    return np.maximum(np.sin(np.pi * x), 0.0)[None, :], x, dx
+
+
+def composite_wave(n: int):
+    """Gaussian, square wave, triangle and semi-ellipse (Eq. (sca_ini_4), TEST 1) on (-1, 1),
+    periodic; z = -0.7, delta = 0.005, beta = log 2 / (36 delta^2), a = 0.5, alpha = 10."""
+    x, dx = grid_1d(n, -1.0, 1.0, periodic=True)
+    return composite_wave_at(x)[None, :], x, dx
+
+
+def composite_wave_at(x):
+    z, d, a, al = -0.7, 0.005, 0.5, 10.0
+    beta = np.log(2.0) / (36.0 * d * d)
+    G = lambda zz: np.exp(-beta * (x - zz) ** 2)
+    F = lambda aa: np.sqrt(np.maximum(1.0 - al * al * (x - aa) ** 2, 0.0))
+    u = np.zeros_like(x)
+    m = (x >= -0.8) & (x <= -0.6)
+    u[m] = ((G(z - d) + 4.0 * G(z) + G(z + d)) / 6.0)[m]
+    u[(x >= -0.4) & (x <= -0.2)] = 1.0
+    m = (x >= 0.0) & (x <= 0.2)
+    u[m] = (1.0 - np.abs(10.0 * (x - 0.1)))[m]
+    m = (x >= 0.4) & (x <= 0.6)
+    u[m] = ((F(a - d) + 4.0 * F(a) + F(a + d)) / 6.0)[m]
+    return u
+
+
+def burgers_sine(n: int, shift=0.0, sign=-1.0):
+    """Burgers data of TEST 2: u0 = -sin(pi x) (Eq. (bur_ini_1)) or 1/2 + sin(pi x)
+    (Eq. (bur_ini_2), shift = 0.5, sign = 1) on (-1, 1), periodic."""
+    x, dx = grid_1d(n, -1.0, 1.0, periodic=True)
+    return (shift + sign * np.sin(np.pi * x))[None, :], x, dx
+
+
+def lax(n: int, lo=-5.0, hi=5.0):
+    """Lax's problem (Eq. (lax_prob), TEST 3): (0.445, 0.698, 3.528) | (0.5, 0, 0.571) at 0."""
+    x, dx = grid_1d(n, lo, hi, periodic=False)
+    left = x < 0.0
+    return cons_1d(np.where(left, 0.445, 0.5), np.where(left, 0.698, 0.0), np.where(left, 3.528, 0.571)), x, dx
+
+
+def shu_osher(n: int, lo=-5.0, hi=5.0):
+    """Shu-Osher shock / density-wave interaction (Eq. (shock_den_prob), TEST 4):
+    (3.857143, 2.629369, 31/3) on (-5, -4), (1 + 0.2 sin 5x, 0, 1) beyond, zero gradient."""
+    x, dx = grid_1d(n, lo, hi, periodic=False)
+    left = x < -4.0
+    rho = np.where(left, 3.857143, 1.0 + 0.2 * np.sin(5.0 * x))
+    return cons_1d(rho, np.where(left, 2.629369, 0.0), np.where(left, 31.0 / 3.0, 1.0)), x, dx
+
+
+def riemann_123(n: int, lo=-5.0, hi=5.0):
+    """The 123 problem as printed (Eq. (123_prob), TEST 3): (1, -2, 0.4) | (1, 2, 0.4) at 0."""
+    x, dx = grid_1d(n, lo, hi, periodic=False)
+    left = x < 0.0
+    return cons_1d(np.ones(n), np.where(left, -2.0, 2.0), np.full(n, 0.4)), x, dx

@@ -474,3 +474,124 @@ def test_blast_waves_against_exact_riemann_solutions(oracle):
             for c in (0, 2):
                 assert abs(r[c].sum() - U[c].sum()) <= 1e-13 * np.abs(U[c]).sum(), (n, c)
     assert errs[0] > errs[1] > errs[2], errs
+
+
+# ---------------------------------------------------------------------------------------------
+# The remaining 1D validation set (Sec. 3.3 resolution test, Sec. 4.1 TESTs 1-2, Sec. 4.2 TESTs 3-4)
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("name", ["lax", "123"])
+def test_lax_and_123_against_exact_solutions(oracle, name):
+    """Lax's problem (alpha_R = 10, t = 1.3) and the 123 problem (alpha_R = 50, t = 1), TEST 3,
+    transmissive ends: L1 density error against the exact Riemann solution falls with N at a
+    rate of a shock-capturing scheme, and the density has no new extrema (TV within 5%)."""
+    O = oracle
+    if name == "lax":
+        make, left, right, t_end, aR = W.lax, (0.445, 0.698, 3.528), (0.5, 0.0, 0.571), 1.3, 10.0
+    else:
+        make, left, right, t_end, aR = W.riemann_123, (1.0, -2.0, 0.4), (1.0, 2.0, 0.4), 1.0, 50.0
+    errs = []
+    for n in (150, 300, 600):
+        U, x, dx = make(n)
+        r, t, _ = O.run(O.problem(O.FLUX_EULER1D, bc=O.BC_OUTFLOW, alpha_R=aR), U, dx, cfl=0.5, t_final=t_end)
+        assert t == t_end and np.isfinite(r).all() and r[0].min() > 0.0
+        rho_ex, _, _ = O.riemann_sample(left, right, x, 0.0, t_end)
+        errs.append(dx * np.abs(r[0] - rho_ex).sum())
+        assert np.abs(np.diff(r[0])).sum() <= 1.05 * np.abs(np.diff(rho_ex)).sum()
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(orders > 0.4), (errs, orders)
+
+
+def _burgers_exact(x, t, shift, sign):
+    """Entropy solution of Burgers' equation with u0 = shift + sign sin(pi x), periodic on
+    (-1, 1), away from the shock: Galilean shift by `shift`, then the characteristic
+    xi + sign t sin(pi xi) = x' solved on the branch where that map is increasing."""
+    xp = np.mod(x - shift * t + 1.0, 2.0) - 1.0  # frame moving with the mean
+    if sign < 0:  # -sin(pi x): shock at x' = 0, odd solution; use x' in (0, 1]
+        s = np.sign(xp)
+        a = np.abs(xp)
+        lo = np.full_like(a, np.arccos(1.0 / (np.pi * t)) / np.pi if np.pi * t > 1 else 0.0)
+        hi = np.ones_like(a)
+        g = lambda xi: xi - t * np.sin(np.pi * xi)
+    else:  # sin(pi x): shock at x' = +-1; x' in (-1, 1)
+        s = np.ones_like(xp)
+        a = xp
+        c = np.arccos(-1.0 / (np.pi * t)) / np.pi if np.pi * t > 1 else 1.0
+        lo, hi = np.full_like(a, -c), np.full_like(a, c)
+        g = lambda xi: xi + t * np.sin(np.pi * xi)
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        left = g(mid) < a
+        lo = np.where(left, mid, lo)
+        hi = np.where(left, hi, mid)
+    xi = 0.5 * (lo + hi)
+    return shift + s * sign * np.sin(np.pi * xi), xp
+
+
+@pytest.mark.parametrize("case", [(0.0, -1.0, 1.5), (0.5, 1.0, 0.55)], ids=["-sin", "1/2+sin"])
+def test_burgers_against_characteristics(oracle, case):
+    """TEST 2 (Burgers, periodic, alpha_R = 50): u0 = -sin(pi x) at t = 1.5 and 1/2 + sin(pi x)
+    at t = 0.55, both after the shock has formed.  Away from the shock (0.15 off it) the
+    solution matches the characteristic solution, with an error that falls with N; the mean
+    is conserved to round-off (periodic, telescoping fluxes)."""
+    O = oracle
+    shift, sign, t_end = case
+    errs = []
+    for n in (100, 200, 400):
+        U, x, dx = W.burgers_sine(n, shift, sign)
+        r, t, _ = O.run(O.problem(O.FLUX_BURGERS, bc=O.BC_PERIODIC), U, dx, cfl=0.5, t_final=t_end)
+        assert t == t_end
+        assert abs(r.sum() - U.sum()) <= 1e-12 * np.abs(U).sum()
+        ex, xp = _burgers_exact(x, t_end, shift, sign)
+        far = (np.abs(xp) > 0.15) if sign < 0 else (np.abs(np.abs(xp) - 1.0) > 0.15)
+        errs.append(np.abs(r[0] - ex)[far].max())
+    assert errs[0] > errs[1] > errs[2] and errs[2] < 1e-4, errs
+
+
+def test_resolution_test_against_exact_translation(oracle):
+    """u0 = max(sin pi x, 0) (Eq. (sca_ini_3)), advection to t = 2.4, CFL 0.4: the L1 error
+    against the exact translation falls with N at better than first order (the kinks at the
+    critical points limit the rate)."""
+    O = oracle
+    errs = []
+    for n in (100, 200, 400):
+        U, x, dx = W.sine_max(n)
+        r, t, _ = O.run(O.problem(O.FLUX_ADVECTION, bc=O.BC_PERIODIC), U, dx, cfl=0.4, t_final=2.4)
+        ex = np.maximum(np.sin(np.pi * (x - 2.4)), 0.0)
+        errs.append(dx * np.abs(r[0] - ex).sum())
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(orders > 1.2), (errs, orders)
+
+
+def test_composite_wave_against_exact_translation(oracle):
+    """TEST 1: Gaussian, square, triangle and semi-ellipse (Eq. (sca_ini_4)), advection to
+    t = 6.3 (N = 400 in the paper): the L1 error against the exact translation falls with N,
+    and from N = 200 on the solution keeps within the data's range up to 2% overshoot."""
+    O = oracle
+    errs = []
+    for n in (100, 200, 400):
+        U, x, dx = W.composite_wave(n)
+        r, t, _ = O.run(O.problem(O.FLUX_ADVECTION, bc=O.BC_PERIODIC), U, dx, cfl=0.4, t_final=6.3)
+        ex = W.composite_wave_at(np.mod(x - 6.3 + 1.0, 2.0) - 1.0)
+        errs.append(dx * np.abs(r[0] - ex).sum())
+        if n >= 200:
+            assert r.min() > -0.01 and r.max() < 1.02
+    assert errs[0] > errs[1] > errs[2], errs
+
+
+def test_shu_osher_converges(oracle):
+    """TEST 4 (Shu-Osher, t = 1.8, zero gradient, alpha_R = 50): no closed form; the density on
+    200 and 400 cells approaches the oracle's 1600-cell solution (sampled at the coarse cell
+    centres), and stays positive and finite."""
+    O = oracle
+    P = O.problem(O.FLUX_EULER1D, bc=O.BC_OUTFLOW)
+    Uf, xf, dxf = W.shu_osher(1600)
+    rf, _, _ = O.run(P, Uf, dxf, cfl=0.5, t_final=1.8)
+    diffs = []
+    for n in (200, 400):
+        U, x, dx = W.shu_osher(n)
+        r, t, _ = O.run(P, U, dx, cfl=0.5, t_final=1.8)
+        assert t == 1.8 and np.isfinite(r).all() and r[0].min() > 0.0
+        k = 1600 // n
+        ref = 0.5 * (rf[0][k // 2 - 1::k] + rf[0][k // 2::k])
+        diffs.append(dx * np.abs(r[0] - ref).sum())
+    assert diffs[1] < 0.8 * diffs[0], diffs
