@@ -128,3 +128,36 @@ def test_implosion_keeps_its_symmetry_on_the_paper_grid(wtlib, oracle):
         u, t, s = _run(b, gp, U, grid, cfl=0.5, t_final=tf)
         assert t == tf and np.isfinite(u).all()
         assert np.array_equal(u, _transpose(u)), (mode, np.abs(u - _transpose(u)).max())
+
+
+VALIDATION = [
+    # (name, flux, workload, bc, alpha_R, cfl, t_final, lo, hi)
+    ("resolution-max-sin-N200", 0, lambda: W.sine_max(200), 0, 50.0, 0.4, 2.4, -1.0, 1.0),
+    ("composite-wave-N400", 0, lambda: W.composite_wave(400), 0, 50.0, 0.4, 6.3, -1.0, 1.0),
+    ("burgers-minus-sin-N200", 1, lambda: W.burgers_sine(200, 0.0, -1.0), 0, 50.0, 0.5, 1.5, -1.0, 1.0),
+    ("burgers-half-plus-sin-N200", 1, lambda: W.burgers_sine(200, 0.5, 1.0), 0, 50.0, 0.5, 0.55, -1.0, 1.0),
+    ("sod-N300", 2, lambda: W.sod(300), 1, 50.0, 0.5, 1.7, -5.0, 5.0),
+    ("lax-N300", 2, lambda: W.lax(300), 1, 10.0, 0.5, 1.3, -5.0, 5.0),
+    ("123-N300", 2, lambda: W.riemann_123(300), 1, 50.0, 0.5, 1.0, -5.0, 5.0),
+    ("shu-osher-N400", 2, lambda: W.shu_osher(400), 1, 50.0, 0.5, 1.8, -5.0, 5.0),
+]
+
+
+@pytest.mark.parametrize("case", VALIDATION, ids=[c[0] for c in VALIDATION])
+def test_validation_set_matches_the_oracle(wtlib, oracle, case):
+    """The paper's 1D validation problems on its grids to its final times: strict mode bitwise
+    equal to the oracle (same step count, same t), fast mode within the L1 tolerance."""
+    b, O = wtlib, oracle
+    name, flux, make, bc, aR, cfl, tf, lo, hi = case
+    U, x, dx = make()
+    n = U.shape[1]
+    op = O.problem(flux, bc=bc, alpha_R=aR)
+    ref, t_ref, s_ref = O.run(op, U, dx, cfl=cfl, t_final=tf)
+    grid = b.grid_1d(n, lo, hi)
+    u, t, s = _run(b, b.problem(flux, bc=bc, mode=b.WT_MODE_STRICT, alpha_R=aR), U, grid, cfl=cfl, t_final=tf)
+    assert t == t_ref == tf and s == s_ref
+    assert np.array_equal(u, ref), np.abs(u - ref).max()
+    u, t, s = _run(b, b.problem(flux, bc=bc, mode=b.WT_MODE_FAST, alpha_R=aR), U, grid, cfl=cfl, t_final=tf)
+    assert abs(t - tf) <= 1e-14 * tf
+    l1 = dx * np.abs(u - ref).sum(axis=1)
+    assert np.all(l1 <= SHOCK_L1_TOL * np.maximum(1.0, dx * np.abs(ref).sum(axis=1))), l1
