@@ -1231,16 +1231,38 @@ int weno_theta_adjoint(const wt_problem* prob, const wt_grid* grid, int32_t npro
   (void)nr;
   const int grid_f = batched_grid_size(prob, 127, nf, dev);
 
-  // ---- forward pass with checkpoints
+  // Steps of one segment from segu(0, 0), keeping u^n, u^(1), u^(2) of every step and the
+  // alphas and dt each stage used; the last step's u^{n+1} goes to final_out (if not null).
+  auto record_segment = [&](int64_t kseg, double* final_out) -> int {
+    for (int64_t k = 0; k < kseg; ++k) {
+      double* ra = rec_a + (size_t)k * 3 * 4 * nprob;
+      WT_CUDA(launch_adj_record(ctl, 0, ra, nullptr, nprob, st));
+      WT_CUDA(launch_batched_stage(prob, STAGE_RK1, 127, bargs(segu(k, 0), nullptr, segu(k, 1), tiles_f, nf), grid_f, st));
+      WT_CUDA(launch_adj_record(ctl, 1, ra + 4 * nprob, rec_dt + (size_t)k * nprob, nprob, st));
+      WT_CUDA(launch_batched_stage(prob, STAGE_RK2, 127, bargs(segu(k, 1), segu(k, 0), segu(k, 2), tiles_f, nf), grid_f, st));
+      WT_CUDA(launch_adj_record(ctl, 2, ra + 8 * nprob, nullptr, nprob, st));
+      double* out = (k + 1 < kseg) ? segu(k + 1, 0) : final_out;
+      if (out) WT_CUDA(launch_batched_stage(prob, STAGE_RK3, 127, bargs(segu(k, 2), segu(k, 0), out, tiles_f, nf), grid_f, st));
+    }
+    return WT_OK;
+  };
+
+  // ---- forward pass with checkpoints.  The last segment runs recording: its stage states
+  // and alphas are what the reverse sweep starts from, so it is never recomputed.
   const int K = checkpoint_every;
   const int64_t S = (n_steps + K - 1) / K;
+  const int64_t last0 = (S > 0) ? (S - 1) * K : 0;  // first step of the last segment
   {
     BatchArgs a3[3] = {bargs(Un, nullptr, U1, tiles_f, nf), bargs(U1, Un, U2, tiles_f, nf), bargs(U2, Un, Un, tiles_f, nf)};
     cudaGraphExec_t exec = nullptr;
-    if (n_steps > 0 && (rc = get_batched_graph(prob, dev, 127, grid_f, a3, &exec)) != WT_OK) return rc;
-    for (int64_t step = 0; step < n_steps; ++step) {
+    if (last0 > 0 && (rc = get_batched_graph(prob, dev, 127, grid_f, a3, &exec)) != WT_OK) return rc;
+    for (int64_t step = 0; step < last0; ++step) {
       if (step % K == 0) WT_CUDA(cudaMemcpyAsync(ckpt + (size_t)(step / K) * 3 * P, Un, plane_bytes, cudaMemcpyDeviceToDevice, st));
       WT_CUDA(cudaGraphLaunch(exec, st));
+    }
+    if (n_steps > 0) {
+      WT_CUDA(cudaMemcpyAsync(segu(0, 0), Un, plane_bytes, cudaMemcpyDeviceToDevice, st));
+      if ((rc = record_segment(n_steps - last0, Un)) != WT_OK) return rc;
     }
   }
   {
@@ -1269,18 +1291,11 @@ int weno_theta_adjoint(const wt_problem* prob, const wt_grid* grid, int32_t npro
   const int grid_r = 0;  // resident-CTA count from the occupancy calculator
   for (int64_t sg = S - 1; sg >= 0; --sg) {
     const int64_t kseg = std::min<int64_t>(K, n_steps - sg * K);
-    // recompute the segment, keeping u^n, u^(1), u^(2) of every step and their alphas and dt
-    WT_CUDA(cudaMemcpyAsync(segu(0, 0), ckpt + (size_t)sg * 3 * P, plane_bytes, cudaMemcpyDeviceToDevice, st));
-    if ((rc = init_ctl(segu(0, 0))) != WT_OK) return rc;
-    for (int64_t k = 0; k < kseg; ++k) {
-      double* ra = rec_a + (size_t)k * 3 * 4 * nprob;
-      WT_CUDA(launch_adj_record(ctl, 0, ra, nullptr, nprob, st));
-      WT_CUDA(launch_batched_stage(prob, STAGE_RK1, 127, bargs(segu(k, 0), nullptr, segu(k, 1), tiles_f, nf), grid_f, st));
-      WT_CUDA(launch_adj_record(ctl, 1, ra + 4 * nprob, rec_dt + (size_t)k * nprob, nprob, st));
-      WT_CUDA(launch_batched_stage(prob, STAGE_RK2, 127, bargs(segu(k, 1), segu(k, 0), segu(k, 2), tiles_f, nf), grid_f, st));
-      WT_CUDA(launch_adj_record(ctl, 2, ra + 8 * nprob, nullptr, nprob, st));
-      if (k + 1 < kseg)
-        WT_CUDA(launch_batched_stage(prob, STAGE_RK3, 127, bargs(segu(k, 2), segu(k, 0), segu(k + 1, 0), tiles_f, nf), grid_f, st));
+    // recompute the segment from its checkpoint (the last one was recorded by the forward pass)
+    if (sg < S - 1) {
+      WT_CUDA(cudaMemcpyAsync(segu(0, 0), ckpt + (size_t)sg * 3 * P, plane_bytes, cudaMemcpyDeviceToDevice, st));
+      if ((rc = init_ctl(segu(0, 0))) != WT_OK) return rc;
+      if ((rc = record_segment(kseg, nullptr)) != WT_OK) return rc;
     }
     // reverse the steps of the segment
     for (int64_t k = kseg - 1; k >= 0; --k) {
