@@ -197,6 +197,22 @@ int weno_theta_adjoint(const wt_problem* prob, const wt_grid* grid, int32_t npro
 #define WT_NOALLOC_SCRATCH_BYTES (8u << 20)
 int weno_theta_rhs_noalloc(const wt_problem* prob, const wt_grid* grid, const double* u, double* L, void* stream);
 
+/*
+ * Self-test of the bounded device-side waits that guard the kernels (bulk-copy completion
+ * on an mbarrier, the grid barrier of the persistent kernels).  Not part of the method (the
+ * paper has no counterpart): it lets a caller check, without faulting or hanging the GPU,
+ * that a wait which can never be satisfied gives up and reports WT_ERR_TIMEOUT.
+ *   which         0: wait on a grid counter nobody increments; 1: wait on an mbarrier for
+ *                 16 bulk-copy bytes that are never sent (no copy is issued); 2: a grid-
+ *                 counter wait that is already satisfied.
+ *   limit_cycles  give up after this many SM clock cycles, 1 .. 2^31
+ *   ws, ws_bytes  device scratch of at least 64 bytes, 256-byte aligned (caller-owned)
+ * Synchronises the stream.  Returns WT_ERR_TIMEOUT when the wait gave up (the expected
+ * result for which = 0 and 1), WT_OK when it completed (which = 2), WT_ERR_ARG for bad
+ * arguments; the context stays usable either way.
+ */
+int wt_selftest_wait(int32_t which, int64_t limit_cycles, void* ws, size_t ws_bytes, void* stream);
+
 /* Message describing the last non-OK status returned on the calling thread. */
 const char* wt_last_error(void);
 

@@ -30,6 +30,7 @@ EXPORTED = (
     "wt_adjoint_workspace_bytes",
     "weno_theta_adjoint",
     "weno_theta_rhs_noalloc",
+    "wt_selftest_wait",
     "wt_last_error",
 )
 
@@ -107,6 +108,8 @@ def lib():
     L.weno_theta_adjoint.restype = ctypes.c_int
     L.weno_theta_rhs_noalloc.argtypes = [P(WtProblem), P(WtGrid), vp, vp, vp]
     L.weno_theta_rhs_noalloc.restype = ctypes.c_int
+    L.wt_selftest_wait.argtypes = [ctypes.c_int32, ctypes.c_int64, vp, ctypes.c_size_t, vp]
+    L.wt_selftest_wait.restype = ctypes.c_int
     L.wt_last_error.argtypes = []
     L.wt_last_error.restype = ctypes.c_char_p
     _lib = L
@@ -261,3 +264,10 @@ def alloc_workspace(nbytes, device="cuda"):
     import torch
 
     return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def selftest_wait(which, limit_cycles, ws, stream=None):
+    """Runs one bounded device-side wait that cannot (which 0, 1) or can (which 2) be
+    satisfied; returns the status (WT_ERR_TIMEOUT when the wait gave up, WT_OK)."""
+    wp, _ = _ptr(ws)
+    return lib().wt_selftest_wait(which, limit_cycles, wp, _nbytes(ws), _stream(stream, None, ws))

@@ -1369,4 +1369,23 @@ int weno_theta_adjoint(const wt_problem* prob, const wt_grid* grid, int32_t npro
   return WT_OK;
 }
 
+int wt_selftest_wait(int32_t which, int64_t limit_cycles, void* ws, size_t ws_bytes, void* stream) {
+  if (which < 0 || which > 2) return fail(WT_ERR_ARG, "which = %d outside 0..2", which);
+  if (limit_cycles < 1 || limit_cycles > (1LL << 31)) return fail(WT_ERR_ARG, "limit_cycles outside 1..2^31");
+  int rc, dev;
+  if ((rc = check_ws(ws, ws_bytes, 64, &dev)) != WT_OK) return rc;
+  DeviceGuard guard;
+  if ((rc = guard.enter(dev)) != WT_OK) return rc;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  unsigned long long* word = static_cast<unsigned long long*>(ws);
+  int* result = reinterpret_cast<int*>(static_cast<char*>(ws) + 16);
+  WT_CUDA(cudaMemsetAsync(ws, 0, 64, st));
+  WT_CUDA(launch_selftest_wait(which, word, limit_cycles, result, st));
+  int h = 0;
+  WT_CUDA(cudaMemcpyAsync(&h, result, sizeof(int), cudaMemcpyDeviceToHost, st));
+  WT_CUDA(cudaStreamSynchronize(st));
+  if (h == WT_ERR_TIMEOUT) return fail(WT_ERR_TIMEOUT, "the device-side wait gave up after %lld cycles", (long long)limit_cycles);
+  return h;
+}
+
 }  // extern "C"

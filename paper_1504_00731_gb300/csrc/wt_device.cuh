@@ -83,11 +83,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait: gives up after ~2^31 SM clock cycles (about one second).
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+// Bounded wait: gives up after `limit` SM clock cycles (default 2^31, about one second).
+constexpr long long kWaitLimit = 1LL << 31;
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long limit = kWaitLimit) {
   const long long start = clock64();
   while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - start > (1LL << 31)) return false;
+    if (clock64() - start > limit) return false;
   }
   return true;
 }
@@ -172,12 +173,13 @@ __device__ __forceinline__ void grid_arrive(unsigned long long* ctr) {
 }
 
 // wait for `target` arrivals; false for every thread of the block on timeout
-__device__ __forceinline__ bool grid_wait(const unsigned long long* ctr, unsigned long long target) {
+__device__ __forceinline__ bool grid_wait(const unsigned long long* ctr, unsigned long long target,
+                                          long long limit = kWaitLimit) {
   int bad = 0;
   if (threadIdx.x == 0) {
     const long long start = clock64();
     while (ld_acquire_u64(ctr) < target) {
-      if (clock64() - start > (1LL << 31)) {
+      if (clock64() - start > limit) {
         bad = 1;
         break;
       }

@@ -234,4 +234,30 @@ cudaError_t launch_adj_record(const Ctl* ctl, int slot, double* alpha_out, doubl
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------------------
+// Self-test of the bounded waits: a grid-counter wait on a word nobody increments, an
+// mbarrier wait for bulk-copy bytes that never arrive (no copy is issued, so nothing is in
+// flight when the block leaves), or a grid-counter wait that is already satisfied.
+// ---------------------------------------------------------------------------------------
+__global__ void selftest_wait_kernel(int which, unsigned long long* word, long long limit, int* result) {
+  __shared__ __align__(8) uint64_t bar;
+  bool ok = true;
+  if (which == 0 || which == 2) {
+    ok = grid_wait(word, which == 0 ? 1ull : 0ull, limit);
+  } else {
+    if (threadIdx.x == 0) {
+      mbar_init(&bar, 1);
+      mbar_arrive_expect_tx(&bar, 16u);
+    }
+    __syncthreads();
+    ok = __syncthreads_or(mbar_wait_bounded(&bar, 0u, limit) ? 0 : 1) == 0;
+  }
+  if (threadIdx.x == 0) *result = ok ? WT_OK : WT_ERR_TIMEOUT;
+}
+
+cudaError_t launch_selftest_wait(int which, unsigned long long* word, long long limit, int* result, cudaStream_t st) {
+  selftest_wait_kernel<<<1, 32, 0, st>>>(which, word, limit, result);
+  return cudaGetLastError();
+}
+
 }  // namespace wt

@@ -113,3 +113,12 @@ def test_gravity_is_checked_on_the_host(wtlib):
                             None) == b.WT_ERR_ARG
     ok = b.problem(b.WT_FLUX_EULER2D, bc=b.WT_BC_PERIODIC, bc_y=b.WT_BC_REFLECTIVE, gravity=0.1)
     assert b.workspace_bytes(ok, g2) > 0
+
+
+def test_selftest_wait_checks_arguments_on_the_host(wtlib):
+    b = wtlib
+    L = b.lib()
+    assert L.wt_selftest_wait(7, 1000, None, 0, None) == b.WT_ERR_ARG
+    assert L.wt_selftest_wait(0, 0, None, 0, None) == b.WT_ERR_ARG
+    assert L.wt_selftest_wait(0, 1 << 40, None, 0, None) == b.WT_ERR_ARG
+    assert L.wt_selftest_wait(0, 1000, None, 0, None) == b.WT_ERR_WORKSPACE
