@@ -15,16 +15,24 @@
  *     frozen where the value goes (used to check the discrete adjoint).  R = Cnt
  *     counts the arithmetic operations.
  *
- * Readings of passages where the paper is silent or ambiguous are marked "Reading".
+ * Readings of passages where the paper is silent or ambiguous are marked "Reading".  One
+ * of them fixes the order of two sums the paper does not order: the back-projection adds
+ * the acoustic pair of characteristic fields first, and the 2D projection adds the normal
+ * momentum before the tangential one in both sweeps, so that mirrored or transposed data
+ * give mirrored or transposed results in binary64 too (the symmetry the paper reports for
+ * its Rayleigh-Taylor and implosion tests).
  *
  * Pins (tests/test_oracle_pins.py): the printed errors of Table 1, the closed-form
  * solution of the linear limit, the linear identities of Eqs. (fh_5) and (fh_6), the
  * Taylor expansions printed with Eqs. (be0_cen)-(be3_cen), (tau_5) and (tau_6),
- * exactness on quadratics, conservation, mirror symmetry, Roe's defining property
- * f(b) - f(a) = A(b - a), and the exact Riemann solution (itself pinned by its
- * pressure-function residual, the Rankine-Hugoniot relations and the Riemann
- * invariants).  Parity unpinned: the solution near discontinuities beyond those
- * monotonicity and convergence bounds, and the value alpha_R = 50 on the Euler
+ * exactness on quadratics, conservation, mirror and transpose symmetry, Roe's defining
+ * property f(b) - f(a) = A(b - a), the gravity source (a uniform state, hydrostatic
+ * balance), exact translation (resolution test, composite wave), the characteristic
+ * solution of Burgers' equation away from its shock, and the exact Riemann solution
+ * (itself pinned by its pressure-function residual, the Rankine-Hugoniot relations and
+ * the Riemann invariants) for Sod, Lax, 123 and the early blast waves.  Parity unpinned:
+ * the solution near discontinuities beyond those monotonicity and convergence bounds
+ * (Shu-Osher only by self-convergence), and the value alpha_R = 10 on the seeded Euler
  * workloads (a convention; the paper sets alpha_R per test).
  */
 #include <cmath>
