@@ -15,12 +15,14 @@ struct FluxM {
   static constexpr int m = (FLUX == WT_FLUX_EULER1D) ? 3 : 1;
 };
 
-// Tile geometry: T cells, T + 1 interfaces, m threads per interface (one per field)
-template <int T, int M>
+// Tile geometry: T cells, T + 1 interfaces, m threads per interface (one per field), or with
+// SPLIT = 2 a pair of adjacent threads per (interface, field), one per side of the
+// reconstruction (two warps per SMSP where the tile fills one warp per SMSP)
+template <int T, int M, int SPLIT = 1>
 struct Tile1D {
   static constexpr int W = (T + 9) & ~1;              // staged window: T + 6 cells + alignment slack, even
   static constexpr int NI = T + 1;
-  static constexpr int NT = ((M * NI + 31) / 32) * 32;
+  static constexpr int NT = SPLIT * ((M * NI + 31) / 32) * 32;
   // shared-memory layout in doubles
   static constexpr int kBar = 0;
   static constexpr int kUin = 2;
@@ -158,9 +160,11 @@ __device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long
                                                 double (&alpha)[FluxM<FLUX>::m], double& dt, double* sm,
                                                 const AlphaWait aw) {
   constexpr int M = FluxM<FLUX>::m;
-  using TL = Tile1D<T, M>;
+  // step-blocked tiles split each reconstruction pair over two threads (see phase C1)
+  constexpr int SPLIT = (MODE == kStepBlocked) ? 2 : 1;
+  using TL = Tile1D<T, M, SPLIT>;
   constexpr int W = TL::W, NI = TL::NI, NT = TL::NT;
-  static_assert(NT >= M * NI, "one (interface, field) item per thread");
+  static_assert(NT >= SPLIT * M * NI, "one (interface, field) item per thread (per thread pair with SPLIT = 2)");
   double* s_uin = sm + TL::kUin;
   double* s_un = sm + TL::kUn;
   double* s_f = sm + TL::kF;
@@ -308,16 +312,50 @@ __device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long
   // characteristic field split into the alpha-free products (l.f, l.u), taken first, and the
   // Lax-Friedrichs combination.  A side whose stencil is not restricted (Eq. (be_res)) queues
   // its weight evaluation, which a second pass spreads over full warps instead of diverging
-  // inside the first.
+  // inside the first.  SPLIT = 2: the threads 2k (+ side) and 2k + 1 (- side) share item k;
+  // each takes the products of three of the six stencil cells and the two swap them by a
+  // shuffle, so each thread runs half the chain of the SPLIT = 1 item with the same operations.
   int* s_qn = reinterpret_cast<int*>(sm + TL::kQn);
   double* s_q = sm + TL::kQ;
   int* s_qi = reinterpret_cast<int*>(sm + TL::kQi);
   constexpr int QCAP = TL::QCAP;
-  const bool has_item = tid < M * ni;
-  const int s = has_item ? tid / ni : 0;
-  const int i = tid - s * ni;
+  const int it = (SPLIT == 2) ? (tid >> 1) : tid;
+  const int side2 = (SPLIT == 2) ? (tid & 1) : 0;
+  const bool has_item = it < M * ni;
+  const int s = has_item ? it / ni : 0;
+  const int i = it - s * ni;
+  // pa, pb: (l.f, l.u) of the stencil cells i .. i + 5 (window index), in the order of the
+  // side's stencil with SPLIT = 2 (the - side reads the cells mirrored, Eq. (flux_split_lf))
   double pa[6], pb[6];
-  if (has_item) {
+  if constexpr (SPLIT == 2) {
+    double oa[3] = {0.0, 0.0, 0.0}, ob[3] = {0.0, 0.0, 0.0};
+    if (has_item) {
+      if (FLUX == WT_FLUX_EULER1D) {
+        double l[3] = {s_L[(3 * s) * NI + i], s_L[(3 * s + 1) * NI + i], s_L[(3 * s + 2) * NI + i]};
+#pragma unroll
+        for (int h = 0; h < 3; ++h) {
+          const int k = i + (side2 ? 5 - h : h);
+          double f[3] = {s_f[k], s_f[W + k], s_f[2 * W + k]};
+          double U[3] = {s_uin[off + k], s_uin[W + off + k], s_uin[2 * W + off + k]};
+          MATH::project3_ab(l, f, U, oa[h], ob[h]);
+        }
+      } else {
+#pragma unroll
+        for (int h = 0; h < 3; ++h) {
+          const int k = i + (side2 ? 5 - h : h);
+          MATH::project1_ab(s_f[k], s_uin[off + k], oa[h], ob[h]);
+        }
+      }
+    }
+    // own cells take stencil places 0..2; the partner's, mirrored, places 5..3
+#pragma unroll
+    for (int h = 0; h < 3; ++h) {
+      pa[h] = oa[h];
+      pb[h] = ob[h];
+      pa[5 - h] = __shfl_xor_sync(0xffffffffu, oa[h], 1);
+      pb[5 - h] = __shfl_xor_sync(0xffffffffu, ob[h], 1);
+    }
+  } else if (has_item) {
     if (FLUX == WT_FLUX_EULER1D) {
       double l[3] = {s_L[(3 * s) * NI + i], s_L[(3 * s + 1) * NI + i], s_L[(3 * s + 2) * NI + i]};
 #pragma unroll
@@ -345,39 +383,46 @@ __device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long
       if (aw.clear >= 0 && tid == 0) ctl->dt = dt;
     }
   }
+  // one reconstruction (stencil q) into s_F[dst], or into the queue
+  auto reconstruct = [&](const double* q, const int dst) {
+    if constexpr (MATH::kSplitWeno) {
+      typename MATH::WenoPart w;
+      double out;
+      if (MATH::weno_begin(q, a.eps, a.alpha_R, out, w)) {
+        s_F[dst] = out;
+      } else {
+        const int slot = atomicAdd(s_qn, 1);
+        if (slot < QCAP) {
+#pragma unroll
+          for (int k = 0; k < 4; ++k) s_q[k * QCAP + slot] = w.e[k];
+          s_q[4 * QCAP + slot] = w.tau;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) s_q[(5 + k) * QCAP + slot] = w.fh[k];
+          s_qi[slot] = dst | (w.theta1 ? (1 << 30) : 0);
+        } else {
+          s_F[dst] = MATH::weno_finish(w);
+        }
+      }
+    } else {
+      s_F[dst] = MATH::weno(q, a.eps, a.alpha_R);
+    }
+  };
   if (has_item) {
     const double al = (s == 0) ? alpha[0] : ((s == 1) ? alpha[1] : alpha[M - 1]);
-    double vp[6], vm[6];
+    if constexpr (SPLIT == 2) {
+      double q[6];
 #pragma unroll
-    for (int kk = 0; kk < 6; ++kk) MATH::project_v(pa[kk], pb[kk], al, vp[kk], vm[kk]);
-    double qm[6];
+      for (int kk = 0; kk < 6; ++kk) q[kk] = MATH::project_side(pa[kk], pb[kk], al, side2 != 0);
+      reconstruct(q, side2 * (M * NI) + s * NI + i);
+    } else {
+      double vp[6], vm[6];
 #pragma unroll
-    for (int kk = 0; kk < 6; ++kk) qm[kk] = vm[5 - kk];
+      for (int kk = 0; kk < 6; ++kk) MATH::project_v(pa[kk], pb[kk], al, vp[kk], vm[kk]);
+      double qm[6];
 #pragma unroll
-    for (int side = 0; side < 2; ++side) {
-      const double* q = side ? qm : vp;
-      const int dst = side * (M * NI) + s * NI + i;
-      if constexpr (MATH::kSplitWeno) {
-        typename MATH::WenoPart w;
-        double out;
-        if (MATH::weno_begin(q, a.eps, a.alpha_R, out, w)) {
-          s_F[dst] = out;
-        } else {
-          const int slot = atomicAdd(s_qn, 1);
-          if (slot < QCAP) {
-#pragma unroll
-            for (int k = 0; k < 4; ++k) s_q[k * QCAP + slot] = w.e[k];
-            s_q[4 * QCAP + slot] = w.tau;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) s_q[(5 + k) * QCAP + slot] = w.fh[k];
-            s_qi[slot] = dst | (w.theta1 ? (1 << 30) : 0);
-          } else {
-            s_F[dst] = MATH::weno_finish(w);
-          }
-        }
-      } else {
-        s_F[dst] = MATH::weno(q, a.eps, a.alpha_R);
-      }
+      for (int kk = 0; kk < 6; ++kk) qm[kk] = vm[5 - kk];
+      reconstruct(vp, s * NI + i);
+      reconstruct(qm, M * NI + s * NI + i);
     }
   }
   __syncthreads();
@@ -811,11 +856,11 @@ __device__ __forceinline__ void sb_load_window(const double* un, long long pitch
 }
 
 template <class MATH, int FLUX, int T>
-__global__ void __launch_bounds__(Tile1D<T + 4 * G, FluxM<FLUX>::m>::NT) stepblock1d_kernel(const PersistArgs p) {
+__global__ void __launch_bounds__(Tile1D<T + 4 * G, FluxM<FLUX>::m, 2>::NT) stepblock1d_kernel(const PersistArgs p) {
   constexpr int M = FluxM<FLUX>::m;
   constexpr int E0 = 3 * G;   // halo cells per side at the start of a step
   constexpr int TB = T + 4 * G;  // cells computed in stage 1: T + 2 * (E0 - G)
-  using TL = Tile1D<TB, M>;
+  using TL = Tile1D<TB, M, 2>;
   constexpr int W = TL::W;
   static_assert(W >= T + 2 * E0, "window of a step");
   extern __shared__ __align__(16) double sm[];
@@ -979,7 +1024,7 @@ int persist1d_capacity_t() {
 // Cooperative launch of the step-blocked kernel (grid = number of tiles of T cells)
 template <class MATH, int FLUX, int T>
 cudaError_t launch_stepblock1d_t(const PersistArgs& p, int grid, cudaStream_t st) {
-  using TL = Tile1D<T + 4 * G, FluxM<FLUX>::m>;
+  using TL = Tile1D<T + 4 * G, FluxM<FLUX>::m, 2>;
   static_assert(TL::bytes <= 48 * 1024, "tile exceeds the default dynamic shared memory limit");
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)grid);
@@ -996,7 +1041,7 @@ cudaError_t launch_stepblock1d_t(const PersistArgs& p, int grid, cudaStream_t st
 
 template <class MATH, int FLUX, int T>
 int stepblock1d_capacity_t() {
-  using TL = Tile1D<T + 4 * G, FluxM<FLUX>::m>;
+  using TL = Tile1D<T + 4 * G, FluxM<FLUX>::m, 2>;
   int dev = 0, sms = 0, coop = 0, per = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return 0;

@@ -159,6 +159,10 @@ struct FastMath {
     vp = fma(alpha, b, a);
     vm = fma(-alpha, b, a);
   }
+  // one side of project_v: v+ (minus false) or v- (minus true), the same value
+  __device__ __forceinline__ static double project_side(double a, double b, double alpha, bool minus) {
+    return fma(minus ? -alpha : alpha, b, a);
+  }
 
   // The reconstruction in two parts.  weno_begin evaluates the sub-stencil values, the
   // indicators, tau and the theta switch; a restricted stencil (Eq. (be_res)) finishes there

@@ -121,6 +121,10 @@ struct StrictMath {
     vp = 0.5 * (a + alpha * b);
     vm = 0.5 * (a - alpha * b);
   }
+  // one side of project_v: v+ (minus false) or v- (minus true), the same value
+  __device__ __forceinline__ static double project_side(double a, double b, double alpha, bool minus) {
+    return minus ? 0.5 * (a - alpha * b) : 0.5 * (a + alpha * b);
+  }
 
   // ---- WENO-theta interface value, Eqs. (fh0)-(fh3), (be0_cen)-(be3_cen), (be_res),
   //      (tau_5), (tau_6), (tau_we6), (gam_we6), (om), (fh_nonlinear); q[i] at x_{j-2+i}
