@@ -98,10 +98,16 @@ int check_grid_1d(const wt_problem* p, const wt_grid* g) {
 // padded plane stride: n + 2G rounded up to 32 doubles (256 bytes)
 inline long long plane_pitch(long long n) { return ((n + 2 * G + 31) / 32) * 32; }
 
-// 1D workspace: [Ctl][Un][U1][U2][staging m*n][staging m*n]
+// Most CTAs of a step-blocked launch (one per SM), and the alpha mailbox words they use
+constexpr long long kStepBlockMaxCtas = 1024;
+inline long long stepblock_mailbox_words(long long ctas) { return 3 * 4 * ctas; }
+
+// 1D workspace: [Ctl][alpha mailbox][Un][U1][U2][staging m*n][staging m*n].  The step-blocked
+// kernel keeps its stage values on chip and uses U1, U2 as its halo mailbox.
 struct Layout1D {
-  size_t ctl, un, u1, u2, st_in, st_out, total;
+  size_t ctl, amb, un, u1, u2, st_in, st_out, total;
   long long pitch;
+  long long amb_ctas;  // CTAs the alpha mailbox has room for
 };
 
 Layout1D layout_1d(int m, long long n) {
@@ -109,9 +115,13 @@ Layout1D layout_1d(int m, long long n) {
   L.pitch = plane_pitch(n);
   const size_t plane = (size_t)m * L.pitch * sizeof(double);
   const size_t stage = (size_t)m * n * sizeof(double);
+  // the step-blocked tiles hold at least 27 cells
+  L.amb_ctas = (n + 26) / 27 < kStepBlockMaxCtas ? (n + 26) / 27 : kStepBlockMaxCtas;
   size_t o = 0;
   L.ctl = o;
   o = align_up(o + sizeof(Ctl));
+  L.amb = o;
+  o = align_up(o + (size_t)stepblock_mailbox_words(L.amb_ctas) * sizeof(unsigned long long));
   L.un = o;
   o = align_up(o + plane);
   L.u1 = o;
@@ -857,7 +867,7 @@ int weno_theta_step(const wt_problem* prob, const wt_grid* grid, double* u, doub
   int kind = 0, pgrid = 0;
   if (max_steps > 0) {
     const int cap_sb = strict ? stepblock1d_capacity_strict(prob->flux) : stepblock1d_capacity_fast(prob->flux);
-    if (nsb <= nsm && nsb <= cap_sb) {
+    if (nsb <= nsm && nsb <= cap_sb && nsb <= lay.amb_ctas) {
       kind = 2;
       pgrid = (int)nsb;
     } else {
@@ -871,6 +881,10 @@ int weno_theta_step(const wt_problem* prob, const wt_grid* grid, double* u, doub
   if (kind != 0) {
     PersistArgs pa;
     for (int s = 0; s < 3; ++s) pa.a[s] = a[s];
+    unsigned long long* amb = reinterpret_cast<unsigned long long*>(w + lay.amb);
+    pa.amb = amb;
+    pa.hmb_hi = reinterpret_cast<unsigned long long*>(U1);
+    pa.hmb_lo = reinterpret_cast<unsigned long long*>(U2);
     constexpr int64_t kChunk = 4096;
     int64_t done = 0;
     while (done < max_steps) {
@@ -879,6 +893,10 @@ int weno_theta_step(const wt_problem* prob, const wt_grid* grid, double* u, doub
       pa.n_steps = k;
       WT_CUDA(cudaMemsetAsync(&ctl->gbar, 0, sizeof(unsigned long long) + 4 * sizeof(unsigned int), st));
       if (kind == 2) {
+        // the mailboxes start every launch with tag 0 and parity 0
+        WT_CUDA(cudaMemsetAsync(amb, 0, (size_t)stepblock_mailbox_words(pgrid) * sizeof(unsigned long long), st));
+        WT_CUDA(cudaMemsetAsync(U1, 0, (size_t)m * lay.pitch * sizeof(double), st));
+        WT_CUDA(cudaMemsetAsync(U2, 0, (size_t)m * lay.pitch * sizeof(double), st));
         WT_CUDA(strict ? launch_stepblock1d_strict(prob->flux, pa, pgrid, st)
                        : launch_stepblock1d_fast(prob->flux, pa, pgrid, st));
       } else {

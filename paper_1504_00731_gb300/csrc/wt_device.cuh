@@ -163,6 +163,18 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
   return v;
 }
 
+// Relaxed gpu-scope 8-byte accesses: single-copy atomic and coherent per location, so a
+// reader sees either the old or the new word.  The mailboxes of the step-blocked kernel
+// carry a tag inside each word and need no fence.
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
 // arrival: every thread's earlier stores are ordered before it (CTA barrier, then a gpu fence)
 __device__ __forceinline__ void grid_arrive(unsigned long long* ctr) {
   __syncthreads();

@@ -16,8 +16,8 @@ struct FluxM {
 };
 
 // Tile geometry: T cells, T + 1 interfaces, m threads per interface (one per field), or with
-// SPLIT = 2 a pair of adjacent threads per (interface, field), one per side of the
-// reconstruction (two warps per SMSP where the tile fills one warp per SMSP)
+// SPLIT = 2 (the step-blocked tiles) a pair of adjacent threads per (interface, field), one
+// per side of the reconstruction (two warps per SMSP where the tile fills one warp per SMSP)
 template <int T, int M, int SPLIT = 1>
 struct Tile1D {
   static constexpr int W = (T + 9) & ~1;              // staged window: T + 6 cells + alignment slack, even
@@ -136,24 +136,36 @@ __global__ void __launch_bounds__(256) alpha1d_batched_kernel(const double* __re
 //                 alphas, and only the last stage writes global memory
 enum { kStage = 0, kResident = 1, kStepBlocked = 2 };
 
-// Alphas of the stage still to be produced by the other CTAs: wait for `target` arrivals on
-// ctl->gbar (target 0: the alphas are given), then read ctl->amax[slot]; the CTA with
-// clear >= 0 then zeroes that slot of the ring.  first_stage: the stage opens an RK step,
+// How a step-blocked stage obtains its alphas and hands on its output.  The alphas come
+// from a mailbox of 8-byte words, four per CTA and stage slot: the keys of the CTA's maxima
+// and, at a step's first stage, whether it has seen a failure, each with the step's parity
+// in bit 63.  Every CTA writes its words, then reads every CTA's words of the slot until
+// all carry this step's parity (a word with the other parity is still the previous
+// step's); the words are single-copy atomic, so no fence or arrival counter is needed.
+// clear >= 0 marks the first CTA (it records dt).  first_stage: the stage opens an RK step,
 // whose dt (from these alphas, cfl or dt_fixed, clipped at t_final) is set after the wait.
+// Stage 3 also writes u^{n+1} of the CTA's own cells to the halo mailbox, as two words
+// (high and low 32 bits of the double) tagged with `tag` in their upper 32 bits.
 struct AlphaWait {
   unsigned long long target;
   int slot, clear;
   int first_stage;
   double cfl, dt_fixed, t, t_final;
+  unsigned long long* amb;   // alpha mailbox [3][gridDim.x][4]
+  unsigned long long par;    // parity of the step (0 or 1)
+  unsigned long long* hmb_hi;
+  unsigned long long* hmb_lo;
+  unsigned int tag;
 };
 
 // Phases B-E of one stage over the cells [js, js + Ts) whose window [js - 3, js + Ts + 3) is
 // in shared memory at s_uin[off...] (s_un for stages 2 and 3), with the stage's dt.  The
 // wave speeds of the cells of [own_lo, own_hi) go to the alpha ring: in kStage and kResident
 // those of the stage output (phase E, next slot, atomics at the end of the stage); in
-// kStepBlocked those of the stage input (phase B, this stage's slot, then an arrival on the
-// grid counter by the last warp while the others go on).  Returns false if a wait for the
-// alphas timed out.
+// kStepBlocked those of the stage input (phase B, this stage's slot of the alpha mailbox,
+// written and then gathered by the last warp while the others go on).  Returns false if a
+// wait for the alphas timed out (the flag word then holds 2) or, at the first stage of a
+// step-blocked RK step, if some CTA has seen a failure (flag word 3): the step is not taken.
 template <class MATH, int FLUX, int STAGE, int T, int MODE>
 __device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long long js, const int Ts, const int off,
                                                 const long long own_lo, const long long own_hi,
@@ -216,26 +228,65 @@ __device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long
     }
 #pragma unroll
     for (int f = 0; f < M; ++f) vb[f] = warp_max_key(vb[f]);
-    if (lane == 0) {
+    // publish: words 0..M-1 the keys of this CTA's maxima, word 3 (first stage) its view of
+    // the status, all with the step's parity in bit 63
+    const unsigned long long pbit = aw.par << 63, low63 = ~(1ull << 63);
+    unsigned long long* slot = aw.amb + (size_t)STAGE * 4 * gridDim.x;
+    if (lane < 4) {
+      unsigned long long w = 0ull;
 #pragma unroll
-      for (int f = 0; f < M; ++f) atomicMax(&ctl->amax[STAGE][f], vb[f]);
-      __threadfence();
-      atomicAdd(&ctl->gbar, 1ull);
-      const long long start = clock64();
-      int ok = 1;
-      while (ld_acquire_u64(&ctl->gbar) < aw.target) {
-        if (clock64() - start > (1LL << 31)) {
+      for (int f = 0; f < M; ++f)
+        if (lane == f) w = vb[f];
+      if (lane == 3 && aw.first_stage) w = (__ldcg(&ctl->status) != 0) ? 1ull : 0ull;
+      st_relaxed_u64(slot + 4 * blockIdx.x + lane, w | pbit);
+    }
+    // gather every CTA's words of this slot (lane l: CTAs l, l + 32, ...), bounded wait.  All
+    // loads of a batch are issued before any is tested, so a polling round costs one trip
+    // to L2, however many CTAs a lane covers.
+    constexpr int kPL = 8;  // CTAs per lane in one batch (256 CTAs, more in further batches)
+    unsigned long long mk[M], stv = 0ull;
+#pragma unroll
+    for (int f = 0; f < M; ++f) mk[f] = 0ull;
+    int ok = 1;
+    const long long start = clock64();
+    for (int base = 0; base < (int)gridDim.x && ok; base += 32 * kPL) {
+      unsigned long long w[kPL][4];
+      for (;;) {
+#pragma unroll
+        for (int q = 0; q < kPL; ++q) {
+          const int cb = base + 32 * q + lane;
+#pragma unroll
+          for (int e = 0; e < 4; ++e) w[q][e] = (cb < (int)gridDim.x) ? ld_relaxed_u64(slot + 4 * cb + e) : pbit;
+        }
+        bool ready = true;
+#pragma unroll
+        for (int q = 0; q < kPL; ++q)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) ready = ready && ((w[q][e] ^ pbit) >> 63) == 0ull;
+        if (ready) break;
+        if (clock64() - start > kWaitLimit) {
           ok = 0;
           break;
         }
       }
-      if (ok) {
 #pragma unroll
-        for (int f = 0; f < M; ++f) s_alpha[f] = __ldcg(&ctl->amax[STAGE][f]);
-        if (aw.clear >= 0)
-          for (int e = 0; e < 8; ++e) ctl->amax[aw.clear][e] = 0ull;
+      for (int q = 0; q < kPL; ++q) {
+#pragma unroll
+        for (int f = 0; f < M; ++f) {
+          const unsigned long long k = w[q][f] & low63;
+          mk[f] = (mk[f] < k) ? k : mk[f];
+        }
+        stv |= w[q][3] & low63;
       }
-      *s_aflag = ok ? 1 : 2;
+    }
+    ok = __all_sync(0xffffffffu, ok);
+    const bool stop = __any_sync(0xffffffffu, stv != 0ull) && aw.first_stage;
+#pragma unroll
+    for (int f = 0; f < M; ++f) mk[f] = warp_max_key(mk[f]);
+    if (lane == 0) {
+#pragma unroll
+      for (int f = 0; f < M; ++f) s_alpha[f] = mk[f];
+      *s_aflag = !ok ? 2 : (stop ? 3 : 1);
     }
   } else {
     const int nb = (MODE == kStepBlocked) ? NT - 32 : NT;  // threads of phase B
@@ -347,13 +398,16 @@ __device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long
         }
       }
     }
-    // own cells take stencil places 0..2; the partner's, mirrored, places 5..3
+    // own cells take stencil places 0..2; the partner's, mirrored, places 5..3 (every warp
+    // with items takes part as a whole)
+    if ((tid >> 5) * 32 < SPLIT * M * ni) {
 #pragma unroll
-    for (int h = 0; h < 3; ++h) {
-      pa[h] = oa[h];
-      pb[h] = ob[h];
-      pa[5 - h] = __shfl_xor_sync(0xffffffffu, oa[h], 1);
-      pb[5 - h] = __shfl_xor_sync(0xffffffffu, ob[h], 1);
+      for (int h = 0; h < 3; ++h) {
+        pa[h] = oa[h];
+        pb[h] = ob[h];
+        pa[5 - h] = __shfl_xor_sync(0xffffffffu, oa[h], 1);
+        pb[5 - h] = __shfl_xor_sync(0xffffffffu, ob[h], 1);
+      }
     }
   } else if (has_item) {
     if (FLUX == WT_FLUX_EULER1D) {
@@ -478,6 +532,13 @@ __device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long
           if (!isfinite(v)) flag_error(ctl, WT_ERR_NONPHYSICAL);
           double* o = a.uout + c * a.pitch;
           o[j + G] = v;
+          // the halo mailbox: u^{n+1} for the neighbours' next step, two tagged words
+          {
+            const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+            const unsigned long long tg = (unsigned long long)aw.tag << 32;
+            st_relaxed_u64(aw.hmb_hi + c * a.pitch + j, tg | (b >> 32));
+            st_relaxed_u64(aw.hmb_lo + c * a.pitch + j, tg | (b & 0xffffffffull));
+          }
           // ghost images of this cell in the output
           if (j < G || j >= n - G) {
             const double vr = (c == 1) ? -v : v;
@@ -823,11 +884,16 @@ __global__ void __launch_bounds__(Tile1D<T, FluxM<FLUX>::m>::NT) persist1d_kerne
 // is the halo reload at the start of a step.  The halo cells are computed with exactly the
 // arithmetic, alphas and dt of their owners.  Non-periodic ends: the computed range stops
 // at the boundary and phase B re-images the ghost cells from the stage input.
-// Alphas: phase B of each stage folds the wave speeds of the CTA's own cells of the stage
-// input into the stage's slot and arrives on the grid counter; the CTA waits for all
-// arrivals only after its alpha-free work (cell quantities, Roe matrices, the (l.f, l.u)
-// products), so the reduction over the grid overlaps that work.  dt follows from the alphas
-// of the first stage.  Stop votes and t as in persist1d_kernel.
+// Exchanges go through tagged mailboxes, with no fence, counter or grid barrier per step:
+//   halos   stage 3 writes u^{n+1} of the CTA's own cells as two words tagged with the
+//           step; the next step polls the 9 halo cells per side until their tags match;
+//   alphas  phase B of each stage: the speed warp writes the maxima of the CTA's own cells
+//           of the stage input, tagged with the step's parity, and gathers every CTA's, all
+//           while the other warps do the alpha-free work (cell quantities, Roe matrices,
+//           the (l.f, l.u) products).  dt follows from the alphas of the first stage.
+// Stop decisions: t_final is seen identically by every CTA; a failure seen by any CTA
+// (its status view, published with the first stage's alphas) stops every CTA before it
+// takes that step, so the state in global memory is the last completed step's.
 // ---------------------------------------------------------------------------------------
 template <class MATH, int FLUX, int T>
 __device__ __forceinline__ void sb_load_window(const double* un, long long pitch, long long n, long long x0, int k_lo,
@@ -853,6 +919,51 @@ __device__ __forceinline__ void sb_load_window(const double* un, long long pitch
     s_uin[c * W + k] = v;
     s_un[c * W + k] = v;
   }
+}
+
+// Halo cells of u^n at the start of a step (window positions [0, E0) and [Tc + E0, Tc + 2 E0))
+// from the halo mailbox: words tagged `tag`, polled with a bounded wait.  Ghost cells of a
+// non-periodic end are skipped: phase B re-images them from the stage input.  Returns false
+// for every thread of the block if a wait timed out.
+template <int M>
+__device__ __forceinline__ bool sb_mailbox_halo(const unsigned long long* hi, const unsigned long long* lo,
+                                                long long pitch, long long n, long long x0, int Tc, int E0,
+                                                bool per_lo, bool per_hi, unsigned int tag, double* s_uin,
+                                                double* s_un, int W) {
+  int bad = 0;
+  const int nh = 2 * E0;
+  for (int idx = threadIdx.x; idx < M * nh; idx += blockDim.x) {
+    const int c = idx / nh, h = idx - c * nh;
+    const int k = (h < E0) ? h : Tc + h;
+    const long long x = x0 + k;
+    long long src;
+    if (x < 0) {
+      if (!per_lo) continue;
+      src = ((x % n) + n) % n;
+    } else if (x >= n) {
+      if (!per_hi) continue;
+      src = x % n;
+    } else {
+      src = x;
+    }
+    const unsigned long long* ph = hi + c * pitch + src;
+    const unsigned long long* pl = lo + c * pitch + src;
+    const long long start = clock64();
+    unsigned long long wh, wl;
+    for (;;) {
+      wh = ld_relaxed_u64(ph);
+      wl = ld_relaxed_u64(pl);
+      if ((unsigned int)(wh >> 32) == tag && (unsigned int)(wl >> 32) == tag) break;
+      if (clock64() - start > kWaitLimit) {
+        bad = 1;
+        break;
+      }
+    }
+    const double v = __longlong_as_double((long long)((wh << 32) | (wl & 0xffffffffull)));
+    s_uin[c * W + k] = v;
+    s_un[c * W + k] = v;
+  }
+  return __syncthreads_or(bad) == 0;
 }
 
 template <class MATH, int FLUX, int T>
@@ -901,62 +1012,53 @@ __global__ void __launch_bounds__(Tile1D<T + 4 * G, FluxM<FLUX>::m, 2>::NT) step
     off = (int)(l - G - x0);
   };
 
+  const int* s_aflag = reinterpret_cast<const int*>(sm + TL::kQn) + 1;
   for (long long step = 0;; ++step) {
+    if (step >= p.n_steps || stop || !(t < t_final)) break;
     if (step > 0) {
-      if (step >= p.n_steps) break;
-      // the previous step's last stage: stores of u^n (halos of this step) and stop votes
-      if (!grid_wait(gbar, nbar * nblk)) {
+      // halo cells of u^n: the neighbours' stage-3 words of the previous step
+      if (!sb_mailbox_halo<M>(p.hmb_hi, p.hmb_lo, pitch, n, x0, Tc, E0, per_lo, per_hi, (unsigned int)step, s_uin,
+                              s_un, W)) {
         if (tid == 0) flag_error(ctl, WT_ERR_TIMEOUT);
         return;
       }
-      const int v = (int)((step - 1) % 3);
-      stop = __ldcg(&ctl->vote[v]) != 0;
-      if (first && tid == 0) ctl->vote[(v + 2) % 3] = 0u;
-    }
-    if (step >= p.n_steps || stop || !(t < t_final)) break;
-    if (step > 0) {
-      sb_load_window<MATH, FLUX, T>(p.a[0].uin, pitch, n, x0, 0, E0, per_lo, per_hi, s_uin, s_un, W);
-      sb_load_window<MATH, FLUX, T>(p.a[0].uin, pitch, n, x0, Tc + E0, wcells, per_lo, per_hi, s_uin, s_un, W);
     }
     __syncthreads();
 
+    const unsigned long long par = (unsigned long long)((~step) & 1);  // the mailboxes start zeroed
     double alpha[M], dt = 0.0;
     long long lo;
     int Ts, off;
-    // ---- RK1: alphas of u^n (slot 0) from every CTA's phase B, then dt
+    // ---- RK1: alphas of u^n (slot 0), then dt; a failure seen by any CTA stops here
     range(2 * G, lo, Ts, off);
     if (!stage1d_compute<MATH, FLUX, STAGE_RK1, TB, kStepBlocked>(
             p.a[0], lo, Ts, off, j0, j0 + Tc, alpha, dt, sm,
-            AlphaWait{(++nbar) * nblk, 0, first ? 2 : -1, 1, cfl, dt_fixed, t, t_final})) {
-      if (tid == 0) flag_error(ctl, WT_ERR_TIMEOUT);
+            AlphaWait{0ull, 0, first ? 2 : -1, 1, cfl, dt_fixed, t, t_final, p.amb, par, nullptr, nullptr, 0u})) {
+      if (*s_aflag != 3 && tid == 0) flag_error(ctl, WT_ERR_TIMEOUT);
       return;
     }
     // ---- RK2: alphas of u1 (slot 1)
     range(G, lo, Ts, off);
     if (!stage1d_compute<MATH, FLUX, STAGE_RK2, TB, kStepBlocked>(
             p.a[1], lo, Ts, off, j0, j0 + Tc, alpha, dt, sm,
-            AlphaWait{(++nbar) * nblk, 1, first ? 0 : -1, 0, 0.0, 0.0, 0.0, 0.0})) {
+            AlphaWait{0ull, 1, -1, 0, 0.0, 0.0, 0.0, 0.0, p.amb, par, nullptr, nullptr, 0u})) {
       if (tid == 0) flag_error(ctl, WT_ERR_TIMEOUT);
       return;
     }
-    // ---- RK3: alphas of u2 (slot 2); u^{n+1} of the CTA's cells to global memory
+    // ---- RK3: alphas of u2 (slot 2); u^{n+1} of the CTA's cells to global memory and to the
+    // halo mailbox (tag step + 1)
     range(0, lo, Ts, off);
     if (!stage1d_compute<MATH, FLUX, STAGE_RK3, TB, kStepBlocked>(
             p.a[2], lo, Ts, off, j0, j0 + Tc, alpha, dt, sm,
-            AlphaWait{(++nbar) * nblk, 2, first ? 1 : -1, 0, 0.0, 0.0, 0.0, 0.0})) {
+            AlphaWait{0ull, 2, -1, 0, 0.0, 0.0, 0.0, 0.0, p.amb, par, p.hmb_hi, p.hmb_lo, (unsigned int)(step + 1)})) {
       if (tid == 0) flag_error(ctl, WT_ERR_TIMEOUT);
       return;
     }
     t = t + dt;
-    if (tid == 0) {
-      if (first) {
-        ctl->t = t;
-        ctl->steps = ctl->steps + 1;
-      }
-      if (__ldcg(&ctl->status) != 0) atomicOr(&ctl->vote[(int)(step % 3)], 1u);
+    if (first && tid == 0) {
+      ctl->t = t;
+      ctl->steps = ctl->steps + 1;
     }
-    grid_arrive(gbar);
-    ++nbar;
   }
 }
 

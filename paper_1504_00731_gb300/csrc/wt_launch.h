@@ -28,6 +28,12 @@ struct Stage1DArgs {
 struct PersistArgs {
   Stage1DArgs a[3];
   long long n_steps;
+  // step-blocked kernel only, zeroed before each launch: the alpha mailbox
+  // [3 stages][grid][4] and the halo mailbox (high and low 32-bit halves of u^{n+1} of
+  // every cell, [m][pitch] each, the step's tag in the upper 32 bits of each word)
+  unsigned long long* amb;
+  unsigned long long* hmb_hi;
+  unsigned long long* hmb_lo;
 };
 
 // One problem of a batch: padded storage at poff in the workspace planes, caller storage
