@@ -488,7 +488,7 @@ def run_ours(args):
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
                          "frac": achieved / FP64_PEAK_GFLOPS, "traffic": traffic_per_launch(),
                          "kernel": "stepblock1d_kernel<FastMath, Euler1D, 27> (one cooperative launch per run: "
-                                   f"{RK_STEPS} RK3 steps, 152 CTAs of 27 cells)",
+                                   f"{RK_STEPS} RK3 steps, 152 CTAs of 27 cells, 256 threads each)",
                          "kernel_ms": kernel_ms, "flops_per_launch": flops_per_launch,
                          "peak_source": "152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz (unit counts and max clock)",
                          "hbm": {"achieved_gbs": hbm_gbs, "peak_gbs": hbm_peak, "frac": hbm_gbs / hbm_peak,
