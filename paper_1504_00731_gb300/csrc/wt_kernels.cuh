@@ -482,7 +482,29 @@ __device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long
   __syncthreads();
   if constexpr (MATH::kSplitWeno) {
     const int nq = min(*s_qn, QCAP);  // the same for every thread of the block
-    if (nq > 0) {
+    if (nq > 0 && MODE == kStepBlocked) {
+      // a quad of lanes per queued reconstruction: lane k forms weight k and its term of the
+      // numerator, the quad sums both ((0 + 1) + (2 + 3), the order of weno_finish's
+      // denominator) and its lane 0 divides.  The tiles holding a shock carry the queue, and
+      // every CTA waits for them at the next alpha exchange.
+      for (int base = 0; base < nq; base += NT / 4) {
+        const int t = base + (tid >> 2), k = tid & 3;
+        const bool act = t < nq;  // the same for the four lanes of a quad
+        double wk = 0.0, nk = 0.0;
+        int d = 0;
+        if (act) {
+          const double e[4] = {s_q[t], s_q[QCAP + t], s_q[2 * QCAP + t], s_q[3 * QCAP + t]};
+          d = s_qi[t];
+          MATH::weno_weight(k, e, s_q[4 * QCAP + t], (d >> 30) & 1, s_q[(5 + k) * QCAP + t], wk, nk);
+        }
+        wk += __shfl_xor_sync(0xffffffffu, wk, 1);
+        nk += __shfl_xor_sync(0xffffffffu, nk, 1);
+        wk += __shfl_xor_sync(0xffffffffu, wk, 2);
+        nk += __shfl_xor_sync(0xffffffffu, nk, 2);
+        if (act && k == 0) s_F[d & ((1 << 30) - 1)] = nk / wk;
+      }
+      __syncthreads();
+    } else if (nq > 0) {
       for (int t = tid; t < nq; t += NT) {
         typename MATH::WenoPart w;
 #pragma unroll

@@ -243,8 +243,26 @@ struct FastMath {
     const double w1 = g1 * (w.e[1] + w.tau) * (w.e[0] * p23);
     const double w2 = g2 * (w.e[2] + w.tau) * (p01 * w.e[3]);
     const double w3 = g3 * (w.e[3] + w.tau) * (p01 * w.e[2]);
-    const double num = fma(w3, w.fh[3], fma(w2, w.fh[2], fma(w1, w.fh[1], w0 * w.fh[0])));
+    // numerator and denominator summed in pairs, products rounded on their own: the order
+    // in which a quad of lanes sums them (weno_weight), so every kernel gets the same value
+    const double num = __dadd_rn(__dadd_rn(__dmul_rn(w0, w.fh[0]), __dmul_rn(w1, w.fh[1])),
+                                 __dadd_rn(__dmul_rn(w2, w.fh[2]), __dmul_rn(w3, w.fh[3])));
     return num / ((w0 + w1) + (w2 + w3));
+  }
+
+  // Weight k of Eq. (om) over the common denominator, exactly as weno_finish forms it, and its
+  // term of the numerator; a quad of lanes forms the four and sums them (see stage1d_compute)
+  __device__ __forceinline__ static void weno_weight(int k, const double* e, double tau, bool theta1, double fhk,
+                                                     double& wk, double& nk) {
+    double g0, g1, g2, g3;
+    gammas(theta1, g0, g1, g2, g3);
+    const double gk = k == 0 ? g0 : (k == 1 ? g1 : (k == 2 ? g2 : g3));
+    const double ek = k == 0 ? e[0] : (k == 1 ? e[1] : (k == 2 ? e[2] : e[3]));
+    // the product of the other three: e1 p23, e0 p23, p01 e3, p01 e2
+    const double pa = (k == 0) ? e[1] : ((k == 1) ? e[0] : e[0] * e[1]);
+    const double pb = (k < 2) ? e[2] * e[3] : ((k == 2) ? e[3] : e[2]);
+    wk = gk * (ek + tau) * (pa * pb);
+    nk = __dmul_rn(wk, fhk);
   }
 
   __device__ __forceinline__ static double weno_flags(const double* q, double eps, double alpha_R, bool& restricted_out,
