@@ -183,11 +183,91 @@ struct FastMath {
     g3 = theta1 ? 0.0 : 1.0 / 20.0;
   }
 
+  // restricted stencil: the weights are gamma^theta (Eq. (gam_we6)) and sum_k gamma_k fh_k is
+  // the linear scheme q2 + sum_j c_j (q_{j+1} - q_j) / 60; theta = 1: (-2, 11, 24, -3, 0),
+  // theta = 0: (-1, 7, 30, -7, 1)
+  __device__ __forceinline__ static double linear_theta(double d0, double d1, double d2, double d3, double d4,
+                                                        double q2, bool theta1) {
+    const double c0 = theta1 ? -2.0 / 60.0 : -1.0 / 60.0;
+    const double c1 = theta1 ? 11.0 / 60.0 : 7.0 / 60.0;
+    const double c2 = theta1 ? 24.0 / 60.0 : 30.0 / 60.0;
+    const double c3 = theta1 ? -3.0 / 60.0 : -7.0 / 60.0;
+    const double c4 = theta1 ? 0.0 : 1.0 / 60.0;
+    return fma(c4, d4, fma(c3, d3, fma(c2, d2, fma(c1, d1, c0 * d0)))) + q2;
+  }
+
+  // |x| as the high word of its bit pattern (orders like |x| for finite x; inf and NaN top it)
+  __device__ __forceinline__ static int hw(double x) { return __double2hiint(x) & 0x7fffffff; }
+  // The high 32 bits of a double as a float: its sign, its exponent rebiased and the top 20
+  // bits of its mantissa, so |hi32(x) - x| < 2^-20 |x|; 0 below 2^-126.  Integer pipe only;
+  // the caller keeps |x| < 2^60.
+  __device__ __forceinline__ static float hi32(double x) {
+    const int hi = __double2hiint(x);
+    const int mag = hi & 0x7fffffff;
+    return mag < 0x38100000 ? 0.0f : __int_as_float(((mag - 0x38000000) << 3) | (hi & 0x80000000));
+  }
+
+  // FP32 screen of the two decisions of a stencil: the restriction test of Eq. (be_res) and
+  // theta of Eq. (tau_we6), from the FP64 differences s0..s3, d1..d3 and the large-stencil
+  // terms t5a, t5b, t6a, t6b.  Returns 1 (restricted, theta = 1) or 2 (restricted, theta = 0)
+  // only where an error bound proves that the FP64 evaluation decides the same, else 0.
+  // Bound: each FP32 input is within 2^-20 of its FP64 value, so each indicator computed in
+  // FP32 is within 2^-15 S^2 of its value from the FP64 inputs (S the largest input; at
+  // most 21 * 2^-20 S^2 for beta_3), and tau5, tau6 (sums of squares) within 2.3 * 2^-20 of
+  // theirs; the FP64 evaluation is within a few 2^-53 of the same values.  The restriction
+  // is taken as proven with the indicators moved by 2^-14 S^2 against it and a further
+  // 2^-18 of slack for the FP32 rounding of the test; theta with a gap above 2^-16 of the
+  // larger tau, which must exceed 2^-120 so that subnormal rounding (2^-149 per operation)
+  // stays far below the gap.
+  __device__ __forceinline__ static int screen(double s0, double s1, double s2, double s3, double d1, double d2,
+                                               double d3, double t5a, double t5b, double t6a, double t6b, double eps,
+                                               double alpha_R) {
+    int hm = max(max(max(hw(s0), hw(s1)), max(hw(s2), hw(s3))), max(max(hw(d1), hw(d2)), hw(d3)));
+    hm = max(hm, max(max(hw(t5a), hw(t5b)), max(hw(t6a), hw(t6b))));
+    hm = max(hm, hw(alpha_R));
+    if (hm >= 0x43b00000) return 0;  // some input at or beyond 2^60, or not finite
+    constexpr float F1312 = 13.0f / 12.0f, F1348 = 13.0f / 48.0f;
+    const float a0 = hi32(s0), a1 = hi32(s1), a2 = hi32(s2), a3 = hi32(s3);
+    const float x1 = hi32(d1), x2 = hi32(d2), x3 = hi32(d3);
+    const float e0 = a0 + x1, g3 = fmaf(3.0f, a2, -a3), e3 = a3 - x3, dd = x2 * x2;
+    const float b0 = fmaf(F1312 * a0, a0, e0 * e0);
+    const float b1 = fmaf(F1312 * a1, a1, dd);
+    const float b2 = fmaf(F1312 * a2, a2, dd);
+    const float b3 = fmaf(F1348 * g3, g3, e3 * e3);
+    const float sg = fmaxf(fmaxf(fmaxf(fabsf(a0), fabsf(a1)), fmaxf(fabsf(a2), fabsf(a3))),
+                           fmaxf(fmaxf(fabsf(x1), fabsf(x2)), fabsf(x3)));
+    const float del = 0x1p-14f * (sg * sg);
+    const float bmax = fmaxf(fmaxf(b0, b1), fmaxf(b2, b3)), bmin = fminf(fminf(b0, b1), fminf(b2, b3));
+    const float aR = hi32(alpha_R), ef = hi32(eps);
+    if (!(aR * ef > 1e-30f)) return 0;
+    if (!((bmax + del) < aR * (ef + (bmin - del)) * (1.0f - 0x1p-18f))) return 0;
+    const float u5a = hi32(t5a), u5b = hi32(t5b), u6a = hi32(t6a), u6b = hi32(t6b);
+    const float tau5 = fmaf(F1312 * u5a, u5a, u5b * u5b);
+    const float tau6 = fmaf(F1312 * u6a, u6a, 0.25f * (u6b * u6b));
+    const float tm = fmaxf(tau5, tau6);
+    if (tm > 0x1p-120f && fabsf(tau6 - tau5) > 0x1p-16f * tm) return (tau6 < tau5) ? 2 : 1;
+    // every large-stencil term zero: tau5 = tau6 = 0 in FP64 too, a tie, theta = 1
+    if (((bits(t5a) | bits(t5b) | bits(t6a) | bits(t6b)) << 1) == 0) return 1;
+    return 0;
+  }
+
   __device__ __forceinline__ static bool weno_begin(const double* q, double eps, double alpha_R, double& out,
                                                     WenoPart& w) {
     constexpr double C1312 = 13.0 / 12.0, C1348 = 13.0 / 48.0;
     const double d0 = q[1] - q[0], d1 = q[2] - q[1], d2 = q[3] - q[2], d3 = q[4] - q[3], d4 = q[5] - q[4];
     const double s0 = d1 - d0, s1 = d2 - d1, s2 = d3 - d2, s3 = d4 - d3;
+    // the large-stencil terms of Eqs. (tau_5), (tau_6)
+    const double t5b = s2 - s1;                // -q1 + 3 q2 - 3 q3 + q4
+    const double t5a = fma(-2.0, s1, s0) + s2; // q0 - 4 q1 + 6 q2 - 4 q3 + q4
+    const double t6a = fma(-3.0, t5b, s3 - s0);      // fifth difference
+    const double t6b = (s0 + s3) - (s1 + s2);        // q0 - 3 q1 + 2 q2 + 2 q3 - 3 q4 + q5
+    // the decisions, where FP32 proves them: no FP64 indicator is needed
+    const int scr = screen(s0, s1, s2, s3, d1, d2, d3, t5a, t5b, t6a, t6b, eps, alpha_R);
+    if (scr != 0) {
+      w.theta1 = scr == 1;
+      out = linear_theta(d0, d1, d2, d3, d4, q[2], w.theta1);
+      return true;
+    }
     // Eqs. (be0_cen)-(be3_cen)
     const double e0 = s0 + d1;                 // q0 - 3 q1 + 2 q2
     const double dd = d2 * d2;                 // (q3 - q2)^2, shared by beta_1 and beta_2
@@ -198,10 +278,6 @@ struct FastMath {
     const double b2 = fma(C1312 * s2, s2, dd);
     const double b3 = fma(C1348 * g3, g3, e3 * e3);
     // Eqs. (tau_5), (tau_6)
-    const double t5b = s2 - s1;                // -q1 + 3 q2 - 3 q3 + q4
-    const double t5a = fma(-2.0, s1, s0) + s2; // q0 - 4 q1 + 6 q2 - 4 q3 + q4
-    const double t6a = fma(-3.0, t5b, s3 - s0);      // fifth difference
-    const double t6b = (s0 + s3) - (s1 + s2);        // q0 - 3 q1 + 2 q2 + 2 q3 - 3 q4 + q5
     const double tau5 = fma(C1312 * t5a, t5a, t5b * t5b);
     const double tau6 = fma(C1312 * t6a, t6a, 0.25 * (t6b * t6b));
     // Eq. (tau_we6)
@@ -211,15 +287,7 @@ struct FastMath {
     const double bmax = nmax(nmax(b0, b1), nmax(b2, b3));
     const double bmin = nmin(nmin(b0, b1), nmin(b2, b3));
     if (!(bits(fma(alpha_R, bmin, alpha_R * eps)) < bits(bmax))) {
-      // restricted: the weights are gamma^theta (Eq. (gam_we6)) and sum_k gamma_k fh_k is the
-      // linear scheme q2 + sum_j c_j (q_{j+1} - q_j) / 60; theta = 1: (-2, 11, 24, -3, 0),
-      // theta = 0: (-1, 7, 30, -7, 1)
-      const double c0 = w.theta1 ? -2.0 / 60.0 : -1.0 / 60.0;
-      const double c1 = w.theta1 ? 11.0 / 60.0 : 7.0 / 60.0;
-      const double c2 = w.theta1 ? 24.0 / 60.0 : 30.0 / 60.0;
-      const double c3 = w.theta1 ? -3.0 / 60.0 : -7.0 / 60.0;
-      const double c4 = w.theta1 ? 0.0 : 1.0 / 60.0;
-      out = fma(c4, d4, fma(c3, d3, fma(c2, d2, fma(c1, d1, c0 * d0)))) + q[2];
+      out = linear_theta(d0, d1, d2, d3, d4, q[2], w.theta1);
       return true;
     }
     // Eqs. (fh0)-(fh3) in difference form
