@@ -118,6 +118,16 @@ __device__ __forceinline__ unsigned long long warp_max_key(unsigned long long v)
   return v;
 }
 
+// The same maximum (every lane of a full warp) from two 32-bit warp reductions: the largest
+// high word, then the largest low word among the lanes that hold it.  A shorter dependent
+// chain than five shuffle rounds, for the alpha exchange of the step-blocked kernel.
+__device__ __forceinline__ unsigned long long warp_max_key_redux(unsigned long long v) {
+  const unsigned hi = (unsigned)(v >> 32);
+  const unsigned mh = __reduce_max_sync(0xffffffffu, hi);
+  const unsigned ml = __reduce_max_sync(0xffffffffu, hi == mh ? (unsigned)v : 0u);
+  return ((unsigned long long)mh << 32) | ml;
+}
+
 // Reduces K keys per thread to the block maximum and folds it into dst[k] with one
 // atomicMax per block.  scratch: >= K * 32 doubles of shared memory.
 template <int K>

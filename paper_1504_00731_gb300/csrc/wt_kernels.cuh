@@ -37,12 +37,14 @@ struct Tile1D {
   static constexpr int kHf = kFs + 2 * M * NI;
   static constexpr int kRed = kHf + M * NI;
   static constexpr int kQn = kRed + 4 * 32;      // queue length (int)
-  static constexpr int kQ = kQn + 2;             // queue records [9][QCAP]
-  // queue of reconstructions whose weights are still to be evaluated: one slot per thread,
-  // fewer if the tile would pass 48 KB (the rest evaluate their weights in place)
-  static constexpr int kQFit = ((48 * 1024 / 8 - kQ) * 2) / 19;
+  // queue of reconstructions still to be completed: one slot per thread, fewer if the tile
+  // would pass 48 KB (the rest are completed in place).  A record holds the weights' inputs
+  // (9 doubles), or with SPLIT = 2 a stencil's differences (15 doubles, FastMath::kDeferRec)
+  static constexpr int REC = (SPLIT == 2) ? 15 : 9;
+  static constexpr int kQ = kQn + 2;             // queue records [REC][QCAP]
+  static constexpr int kQFit = ((48 * 1024 / 8 - kQ) * 2) / (2 * REC + 1);
   static constexpr int QCAP = (kQFit < NT ? kQFit : NT) & ~1;
-  static constexpr int kQi = kQ + 9 * QCAP;      // record destinations (int)
+  static constexpr int kQi = kQ + REC * QCAP;    // record destinations (int)
   static constexpr int kTotal = kQi + QCAP / 2;
   static constexpr size_t bytes = sizeof(double) * kTotal;
 };
@@ -227,7 +229,7 @@ __device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long
       }
     }
 #pragma unroll
-    for (int f = 0; f < M; ++f) vb[f] = warp_max_key(vb[f]);
+    for (int f = 0; f < M; ++f) vb[f] = warp_max_key_redux(vb[f]);
     // publish: words 0..M-1 the keys of this CTA's maxima, word 3 (first stage) its view of
     // the status, all with the step's parity in bit 63
     const unsigned long long pbit = aw.par << 63, low63 = ~(1ull << 63);
@@ -282,7 +284,7 @@ __device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long
     ok = __all_sync(0xffffffffu, ok);
     const bool stop = __any_sync(0xffffffffu, stv != 0ull) && aw.first_stage;
 #pragma unroll
-    for (int f = 0; f < M; ++f) mk[f] = warp_max_key(mk[f]);
+    for (int f = 0; f < M; ++f) mk[f] = warp_max_key_redux(mk[f]);
     if (lane == 0) {
 #pragma unroll
       for (int f = 0; f < M; ++f) s_alpha[f] = mk[f];
@@ -439,7 +441,24 @@ __device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long
   }
   // one reconstruction (stencil q) into s_F[dst], or into the queue
   auto reconstruct = [&](const double* q, const int dst) {
-    if constexpr (MATH::kSplitWeno) {
+    if constexpr (MATH::kSplitWeno && MODE == kStepBlocked) {
+      // a stencil the FP32 screen does not settle is deferred whole to the quad pass, so the
+      // long FP64 path never diverges inside the warps of this pass
+      double rec[TL::REC];
+      double out;
+      if (MATH::weno_front(q, a.eps, a.alpha_R, out, rec)) {
+        s_F[dst] = out;
+      } else {
+        const int slot = atomicAdd(s_qn, 1);
+        if (slot < QCAP) {
+#pragma unroll
+          for (int r = 0; r < TL::REC; ++r) s_q[r * QCAP + slot] = rec[r];
+          s_qi[slot] = dst;
+        } else {
+          s_F[dst] = MATH::weno(q, a.eps, a.alpha_R);
+        }
+      }
+    } else if constexpr (MATH::kSplitWeno) {
       typename MATH::WenoPart w;
       double out;
       if (MATH::weno_begin(q, a.eps, a.alpha_R, out, w)) {
@@ -483,25 +502,20 @@ __device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long
   if constexpr (MATH::kSplitWeno) {
     const int nq = min(*s_qn, QCAP);  // the same for every thread of the block
     if (nq > 0 && MODE == kStepBlocked) {
-      // a quad of lanes per queued reconstruction: lane k forms weight k and its term of the
-      // numerator, the quad sums both ((0 + 1) + (2 + 3), the order of weno_finish's
-      // denominator) and its lane 0 divides.  The tiles holding a shock carry the queue, and
-      // every CTA waits for them at the next alpha exchange.
+      // a quad of lanes per deferred stencil (FastMath::weno_back_quad): lane k forms
+      // indicator k and weight k, the quad shares them by shuffles, and its lane 0 holds the
+      // result.  The tiles holding a shock carry the queue, and every CTA waits for them at
+      // the next alpha exchange.
       for (int base = 0; base < nq; base += NT / 4) {
         const int t = base + (tid >> 2), k = tid & 3;
-        const bool act = t < nq;  // the same for the four lanes of a quad
-        double wk = 0.0, nk = 0.0;
-        int d = 0;
-        if (act) {
-          const double e[4] = {s_q[t], s_q[QCAP + t], s_q[2 * QCAP + t], s_q[3 * QCAP + t]};
-          d = s_qi[t];
-          MATH::weno_weight(k, e, s_q[4 * QCAP + t], (d >> 30) & 1, s_q[(5 + k) * QCAP + t], wk, nk);
+        if (t < nq) {  // the same for the four lanes of a quad
+          double rec[TL::REC];
+#pragma unroll
+          for (int r = 0; r < TL::REC; ++r) rec[r] = s_q[r * QCAP + t];
+          const unsigned qmask = 0xfu << (tid & 28);
+          const double out = MATH::weno_back_quad(k, rec, a.eps, a.alpha_R, qmask);
+          if (k == 0) s_F[s_qi[t]] = out;
         }
-        wk += __shfl_xor_sync(0xffffffffu, wk, 1);
-        nk += __shfl_xor_sync(0xffffffffu, nk, 1);
-        wk += __shfl_xor_sync(0xffffffffu, wk, 2);
-        nk += __shfl_xor_sync(0xffffffffu, nk, 2);
-        if (act && k == 0) s_F[d & ((1 << 30) - 1)] = nk / wk;
       }
       __syncthreads();
     } else if (nq > 0) {

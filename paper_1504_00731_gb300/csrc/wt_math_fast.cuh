@@ -302,6 +302,81 @@ struct FastMath {
     return false;
   }
 
+  // ---- The reconstruction in a front and a back half, for the step-blocked kernel.
+  // weno_front takes the differences, the large-stencil terms and the FP32 screen; a screened
+  // stencil finishes there (linear scheme, returns true).  Any other stencil leaves a record of
+  // kDeferRec doubles (d0..d4, s0..s3, t5a, t5b, t6a, t6b, q2, q3) that a quad of lanes
+  // completes in weno_back_quad with the operations of weno_begin's FP64 path and of
+  // weno_finish, so the value is the same as theirs.
+  static constexpr int kDeferRec = 15;
+  __device__ __forceinline__ static bool weno_front(const double* q, double eps, double alpha_R, double& out,
+                                                    double* rec) {
+    const double d0 = q[1] - q[0], d1 = q[2] - q[1], d2 = q[3] - q[2], d3 = q[4] - q[3], d4 = q[5] - q[4];
+    const double s0 = d1 - d0, s1 = d2 - d1, s2 = d3 - d2, s3 = d4 - d3;
+    const double t5b = s2 - s1;
+    const double t5a = fma(-2.0, s1, s0) + s2;
+    const double t6a = fma(-3.0, t5b, s3 - s0);
+    const double t6b = (s0 + s3) - (s1 + s2);
+    const int scr = screen(s0, s1, s2, s3, d1, d2, d3, t5a, t5b, t6a, t6b, eps, alpha_R);
+    if (scr != 0) {
+      out = linear_theta(d0, d1, d2, d3, d4, q[2], scr == 1);
+      return true;
+    }
+    rec[0] = d0; rec[1] = d1; rec[2] = d2; rec[3] = d3; rec[4] = d4;
+    rec[5] = s0; rec[6] = s1; rec[7] = s2; rec[8] = s3;
+    rec[9] = t5a; rec[10] = t5b; rec[11] = t6a; rec[12] = t6b;
+    rec[13] = q[2]; rec[14] = q[3];
+    return false;
+  }
+
+  // Lane k (0..3) of the quad of lanes `qmask` completes a deferred stencil: indicator k
+  // (Eqs. (be0_cen)-(be3_cen)), the four shared by shuffles, tau5, tau6 and theta, the
+  // restriction test, then either the linear scheme or weight k and the quad's sums.  The
+  // result is valid in lane 0 of the quad.  Every lane of the quad must call it.
+  __device__ __forceinline__ static double weno_back_quad(int k, const double* r, double eps, double alpha_R,
+                                                          unsigned qmask) {
+    constexpr double C1312 = 13.0 / 12.0, C1348 = 13.0 / 48.0;
+    const double d0 = r[0], d1 = r[1], d2 = r[2], d3 = r[3], d4 = r[4];
+    const double s0 = r[5], s1 = r[6], s2 = r[7], s3 = r[8];
+    const double t5a = r[9], t5b = r[10], t6a = r[11], t6b = r[12], q2 = r[13], q3 = r[14];
+    const double e0 = s0 + d1;
+    const double g3 = fma(3.0, s2, -s3);
+    const double e3 = s3 - d3;
+    // indicator k as fma(C x, x, y y): (s0, e0), (s1, d2), (s2, d2), (g3, e3) with 13/48 for k = 3
+    const double x = k == 0 ? s0 : (k == 1 ? s1 : (k == 2 ? s2 : g3));
+    const double y = k == 0 ? e0 : (k == 3 ? e3 : d2);
+    const double bk = fma((k == 3 ? C1348 : C1312) * x, x, y * y);
+    const double x1 = __shfl_xor_sync(qmask, bk, 1), x2 = __shfl_xor_sync(qmask, bk, 2),
+                 x3 = __shfl_xor_sync(qmask, bk, 3);
+    // indicator j comes from the lane at xor distance j ^ k
+    const double b0 = k == 0 ? bk : (k == 1 ? x1 : (k == 2 ? x2 : x3));
+    const double b1 = k == 1 ? bk : (k == 0 ? x1 : (k == 3 ? x2 : x3));
+    const double b2 = k == 2 ? bk : (k == 3 ? x1 : (k == 0 ? x2 : x3));
+    const double b3 = k == 3 ? bk : (k == 2 ? x1 : (k == 1 ? x2 : x3));
+    const double tau5 = fma(C1312 * t5a, t5a, t5b * t5b);
+    const double tau6 = fma(C1312 * t6a, t6a, 0.25 * (t6b * t6b));
+    const bool theta1 = !(bits(tau6) < bits(tau5));
+    const double tau = theta1 ? tau5 : tau6;
+    const double bmax = nmax(nmax(b0, b1), nmax(b2, b3));
+    const double bmin = nmin(nmin(b0, b1), nmin(b2, b3));
+    if (!(bits(fma(alpha_R, bmin, alpha_R * eps)) < bits(bmax))) return linear_theta(d0, d1, d2, d3, d4, q2, theta1);
+    // Eqs. (fh0)-(fh3): fh_k = fma(A, X, fma(B, Y, Z))
+    const double A = k == 0 ? 5.0 / 6.0 : (k == 1 ? 1.0 / 6.0 : (k == 2 ? 2.0 / 3.0 : 1.0 / 3.0));
+    const double X = k == 0 ? d1 : (k == 1 ? d1 : (k == 2 ? d2 : d4));
+    const double B = k == 0 ? -1.0 / 3.0 : (k == 1 ? 1.0 / 3.0 : (k == 2 ? -1.0 / 6.0 : -5.0 / 6.0));
+    const double Y = k == 0 ? d0 : (k == 1 ? d2 : d3);
+    const double Z = k == 3 ? q3 : q2;
+    const double fhk = fma(A, X, fma(B, Y, Z));
+    const double e[4] = {eps + b0, eps + b1, eps + b2, eps + b3};
+    double wk, nk;
+    weno_weight(k, e, tau, theta1, fhk, wk, nk);
+    wk += __shfl_xor_sync(qmask, wk, 1);
+    nk += __shfl_xor_sync(qmask, nk, 1);
+    wk += __shfl_xor_sync(qmask, wk, 2);
+    nk += __shfl_xor_sync(qmask, nk, 2);
+    return nk / wk;
+  }
+
   // Eq. (om) over the common denominator prod_l (eps + beta_l)
   __device__ __forceinline__ static double weno_finish(const WenoPart& w) {
     double g0, g1, g2, g3;
