@@ -333,6 +333,18 @@ __device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long
   if (MODE != kStepBlocked) __syncthreads();
   // step-blocked scalar fluxes have no phase C0: the alphas are awaited here
   if (MODE == kStepBlocked && FLUX != WT_FLUX_EULER1D) __syncthreads();
+  // Step-blocked: where the speed warp holds no phase-C1 item (stages whose items fit in the
+  // other warps), phase C0 closes without it, so the other warps' alpha-free products overlap
+  // its gather; it joins them before the alphas are read.  The condition is the same for
+  // every thread of the block.
+  const bool sw_free = MODE == kStepBlocked && SPLIT * M * ni <= NT - 32;
+  auto c0_barrier = [&]() {
+    if (!sw_free) {
+      __syncthreads();
+    } else if ((tid >> 5) != kSW) {
+      named_barrier_sync(2, NT - 32);
+    }
+  };
 
   // ---- C0: Roe average and left eigenvectors per interface (interface i: cells i+2 | i+3);
   // with MATH::kRoeRows one row of the matrix per thread
@@ -348,7 +360,7 @@ __device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long
         for (int e = 0; e < 3; ++e) s_rs[e * NI + i] = rs[e];
       }
     }
-    __syncthreads();
+    c0_barrier();
   } else if (FLUX == WT_FLUX_EULER1D) {
     for (int i = tid; i < ni; i += NT) {
       double L[9], rs[3];
@@ -358,7 +370,7 @@ __device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long
 #pragma unroll
       for (int e = 0; e < 3; ++e) s_rs[e * NI + i] = rs[e];
     }
-    __syncthreads();
+    c0_barrier();
   }
 
   // ---- C1: per (interface, field) reconstruction on both sides.  The projections onto the
@@ -427,7 +439,9 @@ __device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long
     }
   }
   if (MODE == kStepBlocked) {
-    // the speed warp finished before the end of phase C0 (or the barrier after phase B)
+    // the speed warp holds the alphas of every CTA: it finished before the end of phase C0,
+    // or joins the others here
+    if (sw_free) __syncthreads();
     if (*s_aflag != 1) return false;
 #pragma unroll
     for (int f = 0; f < M; ++f) alpha[f] = bits_to_double(s_alpha[f]);
