@@ -199,17 +199,21 @@ int weno_theta_rhs_noalloc(const wt_problem* prob, const wt_grid* grid, const do
 
 /*
  * Self-test of the bounded device-side waits that guard the kernels (bulk-copy completion
- * on an mbarrier, the grid barrier of the persistent kernels).  Not part of the method (the
- * paper has no counterpart): it lets a caller check, without faulting or hanging the GPU,
- * that a wait which can never be satisfied gives up and reports WT_ERR_TIMEOUT.
+ * on an mbarrier, the grid barrier of the persistent kernels, the mailboxes through which
+ * the step-blocked kernel exchanges halos and alphas).  Not part of the method (the paper
+ * has no counterpart): it lets a caller check, without faulting or hanging the GPU, that a
+ * wait which can never be satisfied gives up and reports WT_ERR_TIMEOUT.
  *   which         0: wait on a grid counter nobody increments; 1: wait on an mbarrier for
  *                 16 bulk-copy bytes that are never sent (no copy is issued); 2: a grid-
- *                 counter wait that is already satisfied.
+ *                 counter wait that is already satisfied; 3: wait for halo mailbox words
+ *                 whose step tag never arrives; 4: wait for alpha mailbox words that never
+ *                 carry the step's parity; 5: an alpha mailbox wait on words already
+ *                 published (and their maxima checked).
  *   limit_cycles  give up after this many SM clock cycles, 1 .. 2^31
  *   ws, ws_bytes  device scratch of at least 64 bytes, 256-byte aligned (caller-owned)
  * Synchronises the stream.  Returns WT_ERR_TIMEOUT when the wait gave up (the expected
- * result for which = 0 and 1), WT_OK when it completed (which = 2), WT_ERR_ARG for bad
- * arguments; the context stays usable either way.
+ * result for which = 0, 1, 3 and 4), WT_OK when it completed (which = 2 and 5), WT_ERR_ARG
+ * for bad arguments; the context stays usable either way.
  */
 int wt_selftest_wait(int32_t which, int64_t limit_cycles, void* ws, size_t ws_bytes, void* stream);
 

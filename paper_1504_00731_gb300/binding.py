@@ -267,7 +267,8 @@ def alloc_workspace(nbytes, device="cuda"):
 
 
 def selftest_wait(which, limit_cycles, ws, stream=None):
-    """Runs one bounded device-side wait that cannot (which 0, 1) or can (which 2) be
-    satisfied; returns the status (WT_ERR_TIMEOUT when the wait gave up, WT_OK)."""
+    """Runs one bounded device-side wait that cannot (which 0, 1, 3, 4) or can (which 2, 5)
+    be satisfied (0 grid counter, 1 mbarrier, 3 halo mailbox, 4 and 5 alpha mailbox); returns
+    the status (WT_ERR_TIMEOUT when the wait gave up, WT_OK)."""
     wp, _ = _ptr(ws)
     return lib().wt_selftest_wait(which, limit_cycles, wp, _nbytes(ws), _stream(stream, None, ws))

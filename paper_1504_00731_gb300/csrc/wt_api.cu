@@ -1388,7 +1388,7 @@ int weno_theta_adjoint(const wt_problem* prob, const wt_grid* grid, int32_t npro
 }
 
 int wt_selftest_wait(int32_t which, int64_t limit_cycles, void* ws, size_t ws_bytes, void* stream) {
-  if (which < 0 || which > 2) return fail(WT_ERR_ARG, "which = %d outside 0..2", which);
+  if (which < 0 || which > 5) return fail(WT_ERR_ARG, "which = %d outside 0..5", which);
   if (limit_cycles < 1 || limit_cycles > (1LL << 31)) return fail(WT_ERR_ARG, "limit_cycles outside 1..2^31");
   int rc, dev;
   if ((rc = check_ws(ws, ws_bytes, 64, &dev)) != WT_OK) return rc;
@@ -1397,8 +1397,9 @@ int wt_selftest_wait(int32_t which, int64_t limit_cycles, void* ws, size_t ws_by
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   unsigned long long* word = static_cast<unsigned long long*>(ws);
   int* result = reinterpret_cast<int*>(static_cast<char*>(ws) + 16);
+  unsigned long long* mbox = reinterpret_cast<unsigned long long*>(static_cast<char*>(ws) + 32);  // 4 words
   WT_CUDA(cudaMemsetAsync(ws, 0, 64, st));
-  WT_CUDA(launch_selftest_wait(which, word, limit_cycles, result, st));
+  WT_CUDA(launch_selftest_wait(which, word, mbox, limit_cycles, result, st));
   int h = 0;
   WT_CUDA(cudaMemcpyAsync(&h, result, sizeof(int), cudaMemcpyDeviceToHost, st));
   WT_CUDA(cudaStreamSynchronize(st));

@@ -138,6 +138,60 @@ __global__ void __launch_bounds__(256) alpha1d_batched_kernel(const double* __re
 //                 alphas, and only the last stage writes global memory
 enum { kStage = 0, kResident = 1, kStepBlocked = 2 };
 
+// Gathers the alpha mailbox words of `ncta` CTAs from one stage slot (4 words per CTA) with a
+// bounded wait (`limit` SM clocks) until every word carries the parity bit `pbit`; called by a
+// whole warp.  Lane l takes CTAs l, l + 32, ...; all loads of a batch are issued before any is
+// tested, so a polling round costs one trip to L2 however many CTAs a lane covers.  On return
+// every lane holds the maxima of words 0..M-1 (keys) in mk and the OR of words 3 in stv (its
+// own CTAs' only; the caller reduces it).  Returns 1, or 0 (every lane) if the wait gave up.
+template <int M>
+__device__ __forceinline__ int gather_alpha_words(const unsigned long long* slot, int ncta, unsigned long long pbit,
+                                                  long long limit, unsigned long long (&mk)[M],
+                                                  unsigned long long& stv) {
+  constexpr int kPL = 8;  // CTAs per lane in one batch (256 CTAs, more in further batches)
+  const unsigned long long low63 = ~(1ull << 63);
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int f = 0; f < M; ++f) mk[f] = 0ull;
+  stv = 0ull;
+  int ok = 1;
+  const long long start = clock64();
+  for (int base = 0; base < ncta && ok; base += 32 * kPL) {
+    unsigned long long w[kPL][4];
+    for (;;) {
+#pragma unroll
+      for (int q = 0; q < kPL; ++q) {
+        const int cb = base + 32 * q + lane;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) w[q][e] = (cb < ncta) ? ld_relaxed_u64(slot + 4 * cb + e) : pbit;
+      }
+      bool ready = true;
+#pragma unroll
+      for (int q = 0; q < kPL; ++q)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) ready = ready && ((w[q][e] ^ pbit) >> 63) == 0ull;
+      if (ready) break;
+      if (clock64() - start > limit) {
+        ok = 0;
+        break;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kPL; ++q) {
+#pragma unroll
+      for (int f = 0; f < M; ++f) {
+        const unsigned long long k = w[q][f] & low63;
+        mk[f] = (mk[f] < k) ? k : mk[f];
+      }
+      stv |= w[q][3] & low63;
+    }
+  }
+  ok = __all_sync(0xffffffffu, ok);
+#pragma unroll
+  for (int f = 0; f < M; ++f) mk[f] = warp_max_key_redux(mk[f]);
+  return ok;
+}
+
 // How a step-blocked stage obtains its alphas and hands on its output.  The alphas come
 // from a mailbox of 8-byte words, four per CTA and stage slot: the keys of the CTA's maxima
 // and, at a step's first stage, whether it has seen a failure, each with the step's parity
@@ -232,7 +286,7 @@ __device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long
     for (int f = 0; f < M; ++f) vb[f] = warp_max_key_redux(vb[f]);
     // publish: words 0..M-1 the keys of this CTA's maxima, word 3 (first stage) its view of
     // the status, all with the step's parity in bit 63
-    const unsigned long long pbit = aw.par << 63, low63 = ~(1ull << 63);
+    const unsigned long long pbit = aw.par << 63;
     unsigned long long* slot = aw.amb + (size_t)STAGE * 4 * gridDim.x;
     if (lane < 4) {
       unsigned long long w = 0ull;
@@ -242,49 +296,10 @@ __device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long
       if (lane == 3 && aw.first_stage) w = (__ldcg(&ctl->status) != 0) ? 1ull : 0ull;
       st_relaxed_u64(slot + 4 * blockIdx.x + lane, w | pbit);
     }
-    // gather every CTA's words of this slot (lane l: CTAs l, l + 32, ...), bounded wait.  All
-    // loads of a batch are issued before any is tested, so a polling round costs one trip
-    // to L2, however many CTAs a lane covers.
-    constexpr int kPL = 8;  // CTAs per lane in one batch (256 CTAs, more in further batches)
+    // gather every CTA's words of this slot, bounded wait
     unsigned long long mk[M], stv = 0ull;
-#pragma unroll
-    for (int f = 0; f < M; ++f) mk[f] = 0ull;
-    int ok = 1;
-    const long long start = clock64();
-    for (int base = 0; base < (int)gridDim.x && ok; base += 32 * kPL) {
-      unsigned long long w[kPL][4];
-      for (;;) {
-#pragma unroll
-        for (int q = 0; q < kPL; ++q) {
-          const int cb = base + 32 * q + lane;
-#pragma unroll
-          for (int e = 0; e < 4; ++e) w[q][e] = (cb < (int)gridDim.x) ? ld_relaxed_u64(slot + 4 * cb + e) : pbit;
-        }
-        bool ready = true;
-#pragma unroll
-        for (int q = 0; q < kPL; ++q)
-#pragma unroll
-          for (int e = 0; e < 4; ++e) ready = ready && ((w[q][e] ^ pbit) >> 63) == 0ull;
-        if (ready) break;
-        if (clock64() - start > kWaitLimit) {
-          ok = 0;
-          break;
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < kPL; ++q) {
-#pragma unroll
-        for (int f = 0; f < M; ++f) {
-          const unsigned long long k = w[q][f] & low63;
-          mk[f] = (mk[f] < k) ? k : mk[f];
-        }
-        stv |= w[q][3] & low63;
-      }
-    }
-    ok = __all_sync(0xffffffffu, ok);
+    const int ok = gather_alpha_words<M>(slot, (int)gridDim.x, pbit, kWaitLimit, mk, stv);
     const bool stop = __any_sync(0xffffffffu, stv != 0ull) && aw.first_stage;
-#pragma unroll
-    for (int f = 0; f < M; ++f) mk[f] = warp_max_key_redux(mk[f]);
     if (lane == 0) {
 #pragma unroll
       for (int f = 0; f < M; ++f) s_alpha[f] = mk[f];
@@ -979,7 +994,7 @@ template <int M>
 __device__ __forceinline__ bool sb_mailbox_halo(const unsigned long long* hi, const unsigned long long* lo,
                                                 long long pitch, long long n, long long x0, int Tc, int E0,
                                                 bool per_lo, bool per_hi, unsigned int tag, double* s_uin,
-                                                double* s_un, int W) {
+                                                double* s_un, int W, long long limit = kWaitLimit) {
   int bad = 0;
   const int nh = 2 * E0;
   for (int idx = threadIdx.x; idx < M * nh; idx += blockDim.x) {
@@ -1004,7 +1019,7 @@ __device__ __forceinline__ bool sb_mailbox_halo(const unsigned long long* hi, co
       wh = ld_relaxed_u64(ph);
       wl = ld_relaxed_u64(pl);
       if ((unsigned int)(wh >> 32) == tag && (unsigned int)(wl >> 32) == tag) break;
-      if (clock64() - start > kWaitLimit) {
+      if (clock64() - start > limit) {
         bad = 1;
         break;
       }

@@ -237,26 +237,43 @@ cudaError_t launch_adj_record(const Ctl* ctl, int slot, double* alpha_out, doubl
 // ---------------------------------------------------------------------------------------
 // Self-test of the bounded waits: a grid-counter wait on a word nobody increments, an
 // mbarrier wait for bulk-copy bytes that never arrive (no copy is issued, so nothing is in
-// flight when the block leaves), or a grid-counter wait that is already satisfied.
+// flight when the block leaves), a grid-counter wait that is already satisfied, and the
+// step-blocked kernel's mailbox waits: halo words whose step tag never arrives, alpha words
+// that never carry the step's parity, and alpha words already published.
 // ---------------------------------------------------------------------------------------
-__global__ void selftest_wait_kernel(int which, unsigned long long* word, long long limit, int* result) {
+__global__ void selftest_wait_kernel(int which, unsigned long long* word, unsigned long long* mbox, long long limit,
+                                     int* result) {
   __shared__ __align__(8) uint64_t bar;
+  __shared__ double s_a[32], s_b[32];
   bool ok = true;
   if (which == 0 || which == 2) {
     ok = grid_wait(word, which == 0 ? 1ull : 0ull, limit);
-  } else {
+  } else if (which == 1) {
     if (threadIdx.x == 0) {
       mbar_init(&bar, 1);
       mbar_arrive_expect_tx(&bar, 16u);
     }
     __syncthreads();
     ok = __syncthreads_or(mbar_wait_bounded(&bar, 0u, limit) ? 0 : 1) == 0;
+  } else if (which == 3) {
+    // one periodic cell whose halo words (zeroed: tag 0) are awaited with tag 1
+    ok = sb_mailbox_halo<1>(mbox, mbox + 1, 1, 1, -1, 1, 1, true, true, 1u, s_a, s_b, 16, limit);
+  } else {
+    // one CTA's alpha words: zeroed (parity 0) and awaited with parity 1, or first published
+    // with parity 1 by this warp
+    const unsigned long long pbit = 1ull << 63;
+    if (which == 5 && threadIdx.x < 4) st_relaxed_u64(mbox + threadIdx.x, pbit | (unsigned long long)threadIdx.x);
+    __syncwarp();
+    unsigned long long mk[3], stv;
+    ok = gather_alpha_words<3>(mbox, 1, pbit, limit, mk, stv) != 0;
+    if (ok) ok = mk[0] == 0ull && mk[1] == 1ull && mk[2] == 2ull;  // the published values
   }
   if (threadIdx.x == 0) *result = ok ? WT_OK : WT_ERR_TIMEOUT;
 }
 
-cudaError_t launch_selftest_wait(int which, unsigned long long* word, long long limit, int* result, cudaStream_t st) {
-  selftest_wait_kernel<<<1, 32, 0, st>>>(which, word, limit, result);
+cudaError_t launch_selftest_wait(int which, unsigned long long* word, unsigned long long* mbox, long long limit,
+                                 int* result, cudaStream_t st) {
+  selftest_wait_kernel<<<1, 32, 0, st>>>(which, word, mbox, limit, result);
   return cudaGetLastError();
 }
 

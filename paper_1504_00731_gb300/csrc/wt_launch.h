@@ -153,7 +153,8 @@ cudaError_t launch_adj_apply(const double* uin, long long pitch, const BatchSeg*
 cudaError_t launch_adj_record(const Ctl* ctl, int slot, double* alpha_out, double* dt_out, int nprob, cudaStream_t st);
 int adj_tile_width();
 
-cudaError_t launch_selftest_wait(int which, unsigned long long* word, long long limit, int* result, cudaStream_t st);
+cudaError_t launch_selftest_wait(int which, unsigned long long* word, unsigned long long* mbox, long long limit,
+                                 int* result, cudaStream_t st);
 
 // Records a message for wt_last_error() on the calling thread and returns code.
 int set_last_error(int code, const char* msg);

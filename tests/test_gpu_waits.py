@@ -1,8 +1,8 @@
 """Failure detection without a GPU fault: every device-side wait in the kernels is bounded, and
 a wait that can never be satisfied gives up and reports WT_ERR_TIMEOUT through the status the
 host reads, leaving the context usable.  The waits run out on purpose here (a grid counter no
-block increments, an mbarrier whose bulk-copy bytes are never sent); nothing is left in
-flight and nothing traps."""
+block increments, an mbarrier whose bulk-copy bytes are never sent, mailbox words that never
+take the awaited tag or parity); nothing is left in flight and nothing traps."""
 import numpy as np
 import pytest
 
@@ -20,6 +20,11 @@ def test_unsatisfiable_waits_time_out_and_the_context_survives(wtlib):
     assert "gave up" in b.last_error()
     assert b.selftest_wait(1, limit, ws) == b.WT_ERR_TIMEOUT
     assert b.selftest_wait(2, limit, ws) == b.WT_OK
+    # the step-blocked kernel's mailboxes: halo words whose tag never comes, alpha words that
+    # never take the step's parity, and alpha words already published
+    assert b.selftest_wait(3, limit, ws) == b.WT_ERR_TIMEOUT
+    assert b.selftest_wait(4, limit, ws) == b.WT_ERR_TIMEOUT
+    assert b.selftest_wait(5, limit, ws) == b.WT_OK
     # the context is still usable: a step runs and matches a fresh run
     U, x, dx = W.euler_c2(512, seed=4)
     prob = b.problem(b.WT_FLUX_EULER1D, bc=b.WT_BC_OUTFLOW, alpha_R=W.ALPHA_R_SEEDED)
