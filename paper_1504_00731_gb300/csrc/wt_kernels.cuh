@@ -253,10 +253,10 @@ __device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long
   constexpr bool kNeedUn = (STAGE == STAGE_RK2 || STAGE == STAGE_RK3);
 
   // ---- B: per-cell quantities (step-blocked: also ghost images of the stage input).
-  // Step-blocked: the last warp meanwhile takes the wave speeds of the CTA's own cells, folds
-  // their maxima into this stage's alpha slot, arrives on the grid counter, waits for every
-  // CTA's arrival and leaves the alphas in shared memory (s_alpha, s_aflag), all before the
-  // end of phase C0.  Its lanes release the other warps from phase B first (named barrier 1).
+  // Step-blocked: the last warp (the speed warp) meanwhile takes the wave speeds of the CTA's
+  // own cells, writes their maxima to this stage's slot of the alpha mailbox, gathers every
+  // CTA's words (gather_alpha_words) and leaves the alphas in shared memory (s_alpha,
+  // s_aflag).  Its lanes release the other warps from phase B first (named barrier 1).
   constexpr int kSW = NT / 32 - 1;  // the speed warp (step-blocked)
   unsigned long long* s_alpha = reinterpret_cast<unsigned long long*>(s_red);
   int* s_aflag = reinterpret_cast<int*>(sm + TL::kQn) + 1;
