@@ -203,28 +203,39 @@ def batched_measure(B, dev, steps=20, plain_sample=64):
     finite = bool(torch.isfinite(u).all())
     rng = np.random.default_rng(0)
     sample = rng.choice(len(segs), plain_sample, replace=False)
-    t_p, cells_p = 0.0, 0
-    for p in sample:
-        o, n = int(batch.offsets[p]), int(batch.lengths[p])
-        pb = B.problem(B.WT_FLUX_EULER1D, bc=int(batch.bc[p]), mode=B.WT_MODE_FAST, alpha_R=W.ALPHA_R_SEEDED)
-        g = B.grid_1d(n, -5.0, 5.0)
-        w = B.alloc_workspace(B.workspace_bytes(pb, g), dev)
-        us = u0[:, o:o + n].contiguous()
-        for _ in range(3):
-            B.weno_theta_step(pb, g, us, 0.5, w, max_steps=1)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        B.weno_theta_step(pb, g, us, 0.5, w, max_steps=steps)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        t_p += e0.elapsed_time(e1) * 1e-3
-        cells_p += n
+
+    def per_problem(launch):
+        """Seconds and cells of the sampled problems through weno_theta_step one at a time."""
+        t_p, cells_p = 0.0, 0
+        for p in sample:
+            o, n = int(batch.offsets[p]), int(batch.lengths[p])
+            pb = B.problem(B.WT_FLUX_EULER1D, bc=int(batch.bc[p]), mode=B.WT_MODE_FAST, alpha_R=W.ALPHA_R_SEEDED,
+                           launch=launch)
+            g = B.grid_1d(n, -5.0, 5.0)
+            w = B.alloc_workspace(B.workspace_bytes(pb, g), dev)
+            us = u0[:, o:o + n].contiguous()
+            for _ in range(3):
+                B.weno_theta_step(pb, g, us, 0.5, w, max_steps=1)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            B.weno_theta_step(pb, g, us, 0.5, w, max_steps=steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t_p += e0.elapsed_time(e1) * 1e-3
+            cells_p += n
+        return t_p, cells_p
+
+    t_p, cells_p = per_problem(B.WT_LAUNCH_AUTO)
+    t_s, cells_s = per_problem(B.WT_LAUNCH_STAGES)
     v_b = total * steps / t_b
     v_p = cells_p * steps / t_p
-    small = [p for p in sample if batch.lengths[p] <= 2048]
+    v_s = cells_s * steps / t_s
     return {"value": v_b, "unit": "cell-updates/s", "plain_value": v_p, "batched_over_plain": v_b / v_p,
+            "plain_stages_value": v_s, "batched_over_plain_stages": v_b / v_s,
             "problems": len(segs), "cells": total, "rk_steps_timed": steps, "finite": finite,
-            "plain_sample": f"{plain_sample} seeded problems through weno_theta_step one at a time",
+            "plain_sample": f"{plain_sample} seeded problems through weno_theta_step one at a time: 'plain' with "
+                            "the automatic launch choice (the step-blocked kernel for the small ones), "
+                            "'plain_stages' with one launch of the fused stage kernel per RK stage",
             "roofline_frac_alu": v_b * FLOPS_PER_CELL_UPDATE / 1e9 / FP64_PEAK_GFLOPS,
             "roofline_note": FLOPS_NOTE,
             "workload": "4096 x 1D Euler, N log-uniform in [256, 65536], mixed periodic/outflow, CFL 0.5"}

@@ -70,6 +70,19 @@ typedef enum {
   WT_MODE_STRICT = 1
 } wt_mode;
 
+/* How weno_theta_step advances a 1D grid (the 2D and batched entry points ignore it).  The
+ * results are the same bit for bit; only the launches differ.  The paper has no counterpart:
+ * it lets a caller compare the launch strategies on its own problems. */
+typedef enum {
+  /* chosen from how the grid's tiles fit the device: the step-blocked persistent kernel when
+   * at most one 27-cell (Euler) or 51-cell (scalar) tile per SM is needed, else the
+   * persistent kernel when every tile is co-resident, else the next */
+  WT_LAUNCH_AUTO = 0,
+  /* one launch of the fused RHS + RK stage kernel per stage, replayed from CUDA graphs of
+   * eight RK steps */
+  WT_LAUNCH_STAGES = 1
+} wt_launch;
+
 typedef struct {
   int32_t flux;       /* wt_flux */
   int32_t m;          /* number of components; must match flux (1, 1, 3, 4) */
@@ -80,7 +93,7 @@ typedef struct {
   int32_t bc_lo[2];   /* wt_bc at x = lo for direction x (index 0) and y (index 1) */
   int32_t bc_hi[2];   /* wt_bc at x = hi */
   int32_t mode;       /* wt_mode */
-  int32_t reserved;   /* must be 0 */
+  int32_t launch;     /* wt_launch (weno_theta_step, 1D); 0 = WT_LAUNCH_AUTO */
   double gravity;     /* 2D Euler only: g of the source terms -g rho (y momentum) and -g rho v
                          (energy) of the Rayleigh-Taylor test (TEST 6, Sec. 4.3), gravity along
                          -y; 0 for none.  Must be finite; nonzero for another flux is

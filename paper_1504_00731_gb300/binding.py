@@ -19,6 +19,7 @@ WT_OK, WT_ERR_ARG, WT_ERR_UNSUPPORTED, WT_ERR_CUDA, WT_ERR_NONPHYSICAL, WT_ERR_T
 WT_FLUX_ADVECTION, WT_FLUX_BURGERS, WT_FLUX_EULER1D, WT_FLUX_EULER2D = 0, 1, 2, 3
 WT_BC_PERIODIC, WT_BC_OUTFLOW, WT_BC_REFLECTIVE = 0, 1, 2
 WT_MODE_FAST, WT_MODE_STRICT = 0, 1
+WT_LAUNCH_AUTO, WT_LAUNCH_STAGES = 0, 1
 _M = {WT_FLUX_ADVECTION: 1, WT_FLUX_BURGERS: 1, WT_FLUX_EULER1D: 3, WT_FLUX_EULER2D: 4}
 
 # every entry point declared in include/weno_theta.h
@@ -46,7 +47,7 @@ class WtProblem(ctypes.Structure):
         ("bc_lo", ctypes.c_int32 * 2),
         ("bc_hi", ctypes.c_int32 * 2),
         ("mode", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("launch", ctypes.c_int32),
         ("gravity", ctypes.c_double),
     ]
 
@@ -127,7 +128,7 @@ def _check(status):
 
 
 def problem(flux, gamma=1.4, adv_speed=1.0, eps=1e-10, alpha_R=50.0, bc=WT_BC_PERIODIC, bc_y=None,
-            mode=WT_MODE_FAST, gravity=0.0) -> WtProblem:
+            mode=WT_MODE_FAST, gravity=0.0, launch=0) -> WtProblem:
     p = WtProblem()
     p.flux = flux
     p.m = _M[flux]
@@ -140,7 +141,7 @@ def problem(flux, gamma=1.4, adv_speed=1.0, eps=1e-10, alpha_R=50.0, bc=WT_BC_PE
     ylo, yhi = (by, by) if isinstance(by, int) else by
     p.bc_lo[0], p.bc_hi[0], p.bc_lo[1], p.bc_hi[1] = lo, hi, ylo, yhi
     p.mode = mode
-    p.reserved = 0
+    p.launch = launch
     p.gravity = gravity
     return p
 

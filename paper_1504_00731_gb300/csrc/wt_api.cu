@@ -53,7 +53,7 @@ int check_problem(const wt_problem* p) {
   if (expected_m(p->flux) < 0) return fail(WT_ERR_ARG, "unknown flux %d", p->flux);
   if (p->m != expected_m(p->flux)) return fail(WT_ERR_ARG, "m = %d does not match flux %d", p->m, p->flux);
   if (p->mode != WT_MODE_FAST && p->mode != WT_MODE_STRICT) return fail(WT_ERR_ARG, "unknown mode %d", p->mode);
-  if (p->reserved != 0) return fail(WT_ERR_ARG, "reserved field must be 0");
+  if (p->launch != WT_LAUNCH_AUTO && p->launch != WT_LAUNCH_STAGES) return fail(WT_ERR_ARG, "unknown launch %d", p->launch);
   if (!(p->eps > 0.0) || !std::isfinite(p->eps)) return fail(WT_ERR_ARG, "eps must be positive");
   if (!(p->alpha_R >= 0.0)) return fail(WT_ERR_ARG, "alpha_R must be >= 0");
   if ((p->flux == WT_FLUX_EULER1D || p->flux == WT_FLUX_EULER2D) && !(p->gamma > 1.0))
@@ -865,7 +865,7 @@ int weno_theta_step(const wt_problem* prob, const wt_grid* grid, double* u, doub
   WT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   const long long ntiles = (n + tile - 1) / tile;
   int kind = 0, pgrid = 0;
-  if (max_steps > 0) {
+  if (max_steps > 0 && prob->launch == WT_LAUNCH_AUTO) {
     const int cap_sb = strict ? stepblock1d_capacity_strict(prob->flux) : stepblock1d_capacity_fast(prob->flux);
     if (nsb <= nsm && nsb <= cap_sb && nsb <= lay.amb_ctas) {
       kind = 2;

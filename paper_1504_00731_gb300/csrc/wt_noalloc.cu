@@ -76,7 +76,8 @@ int weno_theta_rhs_noalloc(const wt_problem* prob, const wt_grid* grid, const do
   if (prob->flux != WT_FLUX_ADVECTION && prob->flux != WT_FLUX_BURGERS && prob->flux != WT_FLUX_EULER1D)
     return set_error(WT_ERR_UNSUPPORTED, "weno_theta_rhs_noalloc supports the 1D fluxes only");
   const int m = prob->flux == WT_FLUX_EULER1D ? 3 : 1;
-  if (prob->m != m || grid->ndim != 1 || prob->reserved != 0 || grid->reserved != 0)
+  if (prob->m != m || grid->ndim != 1 || grid->reserved != 0 ||
+      (prob->launch != WT_LAUNCH_AUTO && prob->launch != WT_LAUNCH_STAGES))
     return set_error(WT_ERR_ARG, "inconsistent problem or grid");
   if (prob->mode != WT_MODE_FAST && prob->mode != WT_MODE_STRICT) return set_error(WT_ERR_ARG, "unknown mode");
   if (!(prob->eps > 0.0) || !(prob->alpha_R >= 0.0) || (m == 3 && !(prob->gamma > 1.0)))

@@ -40,7 +40,7 @@ def test_struct_layouts_match_header(wtlib, tmp_path):
         pytest.skip("no host C compiler")
     inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
     fields = {"wt_problem": ("flux", "m", "gamma", "adv_speed", "eps", "alpha_R", "bc_lo", "bc_hi", "mode",
-                             "reserved", "gravity"),
+                             "launch", "gravity"),
               "wt_grid": ("ndim", "reserved", "n", "lo", "hi"),
               "wt_segment": ("offset", "n", "lo", "hi", "bc_lo", "bc_hi")}
     lines = ["#include <stddef.h>", "#include <stdio.h>", "#include <cuda_runtime_api.h>", '#include "weno_theta.h"',

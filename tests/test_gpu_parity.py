@@ -259,3 +259,27 @@ def test_nonphysical_state_is_reported_not_hidden(wtlib):
     U2, _, _ = W.euler_c2(256, seed=3)
     u2 = torch.from_numpy(U2).cuda()
     b.weno_theta_step(prob, g, u2, 0.5, ws, max_steps=3)
+
+
+@pytest.mark.parametrize("mode", ["strict", "fast"])
+def test_launch_strategies_agree_bit_for_bit(wtlib, mode):
+    """weno_theta_step through the step-blocked kernel (the automatic choice for these sizes)
+    and through per-stage launches of the fused stage kernel give the same state, in either
+    arithmetic policy: shock data whose stencils take every path (screened, deferred, weights)."""
+    b = wtlib
+    md = b.WT_MODE_STRICT if mode == "strict" else b.WT_MODE_FAST
+    cases = [(b.WT_FLUX_EULER1D, b.WT_BC_OUTFLOW, W.euler_c2(300, seed=5)[0], -5.0, 5.0),
+             (b.WT_FLUX_EULER1D, b.WT_BC_PERIODIC, W.euler_c2(1000, seed=6)[0], -5.0, 5.0),
+             (b.WT_FLUX_BURGERS, b.WT_BC_PERIODIC, W.advection_ic2(200, 2)[0] + 0.3, -1.0, 1.0)]
+    for flux, bc, U, lo, hi in cases:
+        out = []
+        for launch in (b.WT_LAUNCH_AUTO, b.WT_LAUNCH_STAGES):
+            prob = b.problem(flux, bc=bc, mode=md, alpha_R=W.ALPHA_R_SEEDED, launch=launch)
+            n = U.shape[-1]
+            g = b.grid_1d(n, lo, hi)
+            ws = b.alloc_workspace(b.workspace_bytes(prob, g))
+            u = torch.from_numpy(np.ascontiguousarray(U)).cuda()
+            t, s = b.weno_theta_step(prob, g, u, 0.5, ws, max_steps=40)
+            out.append((u.cpu().numpy(), t, s))
+        assert out[0][2] == out[1][2] == 40 and out[0][1] == out[1][1], (flux, bc)
+        assert np.array_equal(out[0][0], out[1][0]), (flux, bc, np.abs(out[0][0] - out[1][0]).max())
