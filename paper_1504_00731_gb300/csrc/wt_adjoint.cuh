@@ -574,13 +574,19 @@ __global__ void adj_apply_kernel(const double* uin, long long pitch, const Batch
                                  const int* tcount, const double* partial, const double* alpha, const double* dt,
                                  const int* arg, double* ubar, long long ustride, double* dtbar, int final_stage,
                                  double gamma, int nprob) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= nprob) return;
+  // one warp per problem: the lanes sum strided tiles' partials, then a fixed-order shuffle
+  // reduction (deterministic); lane 0 applies the derivatives of the maxima
+  const int p = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (p >= nprob) return;  // the same for the whole warp
   const BatchSeg sg = segs[p];
   const double* u = uin + sg.poff;
   double ab[4] = {0, 0, 0, 0};
-  for (int t = tstart[p]; t < tstart[p] + tcount[p]; ++t)
+  for (int t = tstart[p] + lane; t < tstart[p] + tcount[p]; t += 32)
     for (int e = 0; e < 4; ++e) ab[e] += partial[4 * t + e];
+  for (int o = 16; o > 0; o >>= 1)
+    for (int e = 0; e < 4; ++e) ab[e] += __shfl_xor_sync(0xffffffffu, ab[e], o);
+  if (lane != 0) return;
   for (int s = 0; s < 3; ++s) {
     const int j = arg[4 * p + s];
     if (j < 0 || j >= sg.n) continue;

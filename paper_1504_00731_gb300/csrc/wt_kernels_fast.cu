@@ -224,8 +224,8 @@ cudaError_t launch_adj_apply(const double* uin, long long pitch, const BatchSeg*
                              const int* tcount, const double* partial, const double* alpha, const double* dt,
                              const int* arg, double* ubar, long long ustride, double* dtbar, int final_stage,
                              double gamma, int nprob, cudaStream_t st) {
-  adj_apply_kernel<<<(nprob + 127) / 128, 128, 0, st>>>(uin, pitch, segs, tstart, tcount, partial, alpha, dt, arg, ubar,
-                                                        ustride, dtbar, final_stage, gamma, nprob);
+  adj_apply_kernel<<<(nprob + 3) / 4, 128, 0, st>>>(uin, pitch, segs, tstart, tcount, partial, alpha, dt, arg, ubar,
+                                                    ustride, dtbar, final_stage, gamma, nprob);
   return cudaGetLastError();
 }
 
