@@ -231,8 +231,9 @@ struct AdjTile {
   static constexpr int kW = kHf + 3 * NI;    // [3][T + 2] w = cL dt ubar_out on cells j0-1 .. j0+T
   static constexpr int kHb = kW + 3 * (T + 2);  // [3][NI] hbar
   static constexpr int kLb = kHb + 3 * NI;   // [3 fields][NI][3] adjoint of the stored L rows
-  static constexpr int kG = kLb + 9 * NI;    // [3 fields][NI][36]
-  static constexpr int kRed = kG + 3 * NI * 36;  // 4 * 32
+  static constexpr int kG = kLb + 9 * NI;    // [3 fields][NI][12]: per stencil cell, the adjoints
+                                             // of its projected flux and state (ab, bb)
+  static constexpr int kRed = kG + 3 * NI * 12;  // 4 * 32
   static constexpr int kTotal = kRed + 4 * 32;
   static constexpr size_t bytes = sizeof(double) * kTotal;
 };
@@ -350,13 +351,15 @@ __global__ void __launch_bounds__(AdjTile<T>::NT) adj_stage_kernel(const AdjArgs
     for (int item2 = tid; item2 < 3 * ni; item2 += NT) {
       const int s = item2 / ni, i = item2 - s * ni;
       const double l[3] = {s_L[(3 * s) * NI + i], s_L[(3 * s + 1) * NI + i], s_L[(3 * s + 2) * NI + i]};
-      double vp[6], vm[6], qm[6];
+      double vp[6], vm[6], qm[6], pb[6];
 #pragma unroll
       for (int kk = 0; kk < 6; ++kk) {
         const int k = i + kk;
         const double f[3] = {s_f[k], s_f[W + k], s_f[2 * W + k]};
         const double U[3] = {s_uin[off + k], s_uin[W + off + k], s_uin[2 * W + off + k]};
-        MATH::project3(l, f, U, al[s], vp[kk], vm[kk]);
+        double pa;
+        MATH::project3_ab(l, f, U, pa, pb[kk]);  // the same operations as project3
+        MATH::project_v(pa, pb[kk], al[s], vp[kk], vm[kk]);
       }
 #pragma unroll
       for (int kk = 0; kk < 6; ++kk) qm[kk] = vm[5 - kk];
@@ -365,7 +368,7 @@ __global__ void __launch_bounds__(AdjTile<T>::NT) adj_stage_kernel(const AdjArgs
       s_F[s * NI + i] = Fs;
       const bool owned = (i >= 1) || (j0 == 0);
       if (!owned) continue;
-      double* Gs = s_G + (s * NI + i) * 36;
+      double* Gs = s_G + (s * NI + i) * 12;
       double* Lbs = s_Lb + (s * NI + i) * 3;
       const double u = s_rs[i], H = s_rs[NI + i], c = s_rs[2 * NI + i];
       const double hb[3] = {s_hb[i], s_hb[NI + i], s_hb[2 * NI + i]};
@@ -385,16 +388,16 @@ __global__ void __launch_bounds__(AdjTile<T>::NT) adj_stage_kernel(const AdjArgs
         const double f[3] = {s_f[k], s_f[W + k], s_f[2 * W + k]};
         const double U[3] = {s_uin[off + k], s_uin[W + off + k], s_uin[2 * W + off + k]};
         const double vmb = qmb[5 - kk];
-        const double bq = fma(l[2], U[2], fma(l[1], U[1], l[0] * U[0]));  // stored-L projection of u
+        const double bq = pb[kk];  // stored-L projection of u
         const double abk = MATH::kProj * (vpb[kk] + vmb);
         const double bbk = MATH::kProj * al[s] * (vpb[kk] - vmb);
         ab_alpha = fma(MATH::kProj * bq, vpb[kk] - vmb, ab_alpha);
 #pragma unroll
-        for (int e = 0; e < 3; ++e) {
-          Lb3[e] = fma(abk, f[e], fma(bbk, U[e], Lb3[e]));
-          Gs[kk * 6 + e] = abk * l[e];      // adjoint of the physical flux of stencil cell kk
-          Gs[kk * 6 + 3 + e] = bbk * l[e];  // adjoint of the state of stencil cell kk
-        }
+        for (int e = 0; e < 3; ++e) Lb3[e] = fma(abk, f[e], fma(bbk, U[e], Lb3[e]));
+        // adjoints of the projected flux and state of stencil cell kk; phase D reverse forms
+        // their images under the three fields' L rows
+        Gs[kk] = abk;
+        Gs[6 + kk] = bbk;
       }
 #pragma unroll
       for (int e = 0; e < 3; ++e) Lbs[e] = Lb3[e];
@@ -445,16 +448,24 @@ __global__ void __launch_bounds__(AdjTile<T>::NT) adj_stage_kernel(const AdjArgs
       roe_reverse(Ua, Ubv, s_sr[ka], s_vel[ka], s_H[ka], s_sr[kb], s_vel[kb], s_H[kb], rs, a.gamma, Lb, Rb, Uab, Ubb);
       const long long gi = j0 - 1 + i;
       double* out = a.G + (a.goff[p] + gi + 1) * 36;
+      // the stencil cells' flux and state adjoints: sum over the fields s of ab_s l_s, bb_s l_s
+      double lr[9];
+#pragma unroll
+      for (int e = 0; e < 9; ++e) lr[e] = s_L[e * NI + i];
+      const double* G0 = s_G + (0 * NI + i) * 12;
+      const double* G1 = s_G + (1 * NI + i) * 12;
+      const double* G2 = s_G + (2 * NI + i) * 12;
 #pragma unroll
       for (int kk = 0; kk < 6; ++kk) {
+        const double a0 = G0[kk], a1 = G1[kk], a2 = G2[kk];
+        const double c0 = G0[6 + kk], c1 = G1[6 + kk], c2 = G2[6 + kk];
 #pragma unroll
-        for (int e = 0; e < 6; ++e) {
-          double v = s_G[(0 * NI + i) * 36 + kk * 6 + e];
-          v += s_G[(1 * NI + i) * 36 + kk * 6 + e];
-          v += s_G[(2 * NI + i) * 36 + kk * 6 + e];
-          if (e >= 3 && kk == 2) v += Uab[e - 3];
-          if (e >= 3 && kk == 3) v += Ubb[e - 3];
-          out[kk * 6 + e] = v;
+        for (int e = 0; e < 3; ++e) {
+          out[kk * 6 + e] = fma(a2, lr[6 + e], fma(a1, lr[3 + e], a0 * lr[e]));
+          double v = fma(c2, lr[6 + e], fma(c1, lr[3 + e], c0 * lr[e]));
+          if (kk == 2) v += Uab[e];
+          if (kk == 3) v += Ubb[e];
+          out[kk * 6 + 3 + e] = v;
         }
       }
     }
