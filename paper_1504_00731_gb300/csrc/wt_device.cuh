@@ -184,6 +184,14 @@ __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long
 __device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
   asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
+// Four relaxed 8-byte words from a 32-byte aligned address in one request.  Each word is
+// single-copy atomic on its own; the four are not read as one atomic unit.
+__device__ __forceinline__ void ld_relaxed_v4_u64(const unsigned long long* p, unsigned long long (&w)[4]) {
+  asm volatile("ld.relaxed.gpu.global.v4.u64 {%0,%1,%2,%3}, [%4];"
+               : "=l"(w[0]), "=l"(w[1]), "=l"(w[2]), "=l"(w[3])
+               : "l"(p)
+               : "memory");
+}
 
 // arrival: every thread's earlier stores are ordered before it (CTA barrier, then a gpu fence)
 __device__ __forceinline__ void grid_arrive(unsigned long long* ctr) {

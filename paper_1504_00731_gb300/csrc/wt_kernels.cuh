@@ -140,15 +140,17 @@ enum { kStage = 0, kResident = 1, kStepBlocked = 2 };
 
 // Gathers the alpha mailbox words of `ncta` CTAs from one stage slot (4 words per CTA) with a
 // bounded wait (`limit` SM clocks) until every word carries the parity bit `pbit`; called by a
-// whole warp.  Lane l takes CTAs l, l + 32, ...; all loads of a batch are issued before any is
-// tested, so a polling round costs one trip to L2 however many CTAs a lane covers.  On return
-// every lane holds the maxima of words 0..M-1 (keys) in mk and the OR of words 3 in stv (its
-// own CTAs' only; the caller reduces it).  Returns 1, or 0 (every lane) if the wait gave up.
+// whole warp.  Lane l takes CTAs l, l + 32, ...; a CTA's four words are one 32-byte load
+// (`slot` is 32-byte aligned), and all loads of a round are issued before any is tested, so a
+// polling round costs one trip to L2 however many CTAs a lane covers.  After the first round
+// only the CTAs whose words do not all carry the parity yet are read again.  On return every
+// lane holds the maxima of words 0..M-1 (keys) in mk and the OR of words 3 in stv (its own
+// CTAs' only; the caller reduces it).  Returns 1, or 0 (every lane) if the wait gave up.
 template <int M>
 __device__ __forceinline__ int gather_alpha_words(const unsigned long long* slot, int ncta, unsigned long long pbit,
                                                   long long limit, unsigned long long (&mk)[M],
                                                   unsigned long long& stv) {
-  constexpr int kPL = 8;  // CTAs per lane in one batch (256 CTAs, more in further batches)
+  constexpr int kPL = 5;  // CTAs per lane in one batch (160 CTAs, more in further batches)
   const unsigned long long low63 = ~(1ull << 63);
   const int lane = threadIdx.x & 31;
 #pragma unroll
@@ -158,20 +160,25 @@ __device__ __forceinline__ int gather_alpha_words(const unsigned long long* slot
   const long long start = clock64();
   for (int base = 0; base < ncta && ok; base += 32 * kPL) {
     unsigned long long w[kPL][4];
-    for (;;) {
+    unsigned int need = 0u;  // CTAs of this batch whose words are not all there yet
 #pragma unroll
-      for (int q = 0; q < kPL; ++q) {
-        const int cb = base + 32 * q + lane;
+    for (int q = 0; q < kPL; ++q) {
 #pragma unroll
-        for (int e = 0; e < 4; ++e) w[q][e] = (cb < ncta) ? ld_relaxed_u64(slot + 4 * cb + e) : pbit;
-      }
-      bool ready = true;
+      for (int e = 0; e < 4; ++e) w[q][e] = pbit;
+      if (base + 32 * q + lane < ncta) need |= 1u << q;
+    }
+    while (need != 0u) {
 #pragma unroll
       for (int q = 0; q < kPL; ++q)
+        if (need & (1u << q)) ld_relaxed_v4_u64(slot + 4 * (base + 32 * q + lane), w[q]);
+#pragma unroll
+      for (int q = 0; q < kPL; ++q) {
+        bool ready = true;
 #pragma unroll
         for (int e = 0; e < 4; ++e) ready = ready && ((w[q][e] ^ pbit) >> 63) == 0ull;
-      if (ready) break;
-      if (clock64() - start > limit) {
+        if (ready) need &= ~(1u << q);
+      }
+      if (need != 0u && clock64() - start > limit) {
         ok = 0;
         break;
       }
@@ -1031,8 +1038,9 @@ __device__ __forceinline__ bool sb_mailbox_halo(const unsigned long long* hi, co
   return __syncthreads_or(bad) == 0;
 }
 
+// one CTA per SM (the launch checks that the grid is co-resident)
 template <class MATH, int FLUX, int T>
-__global__ void __launch_bounds__(Tile1D<T + 4 * G, FluxM<FLUX>::m, 2>::NT) stepblock1d_kernel(const PersistArgs p) {
+__global__ void __launch_bounds__(Tile1D<T + 4 * G, FluxM<FLUX>::m, 2>::NT, 1) stepblock1d_kernel(const PersistArgs p) {
   constexpr int M = FluxM<FLUX>::m;
   constexpr int E0 = 3 * G;   // halo cells per side at the start of a step
   constexpr int TB = T + 4 * G;  // cells computed in stage 1: T + 2 * (E0 - G)
