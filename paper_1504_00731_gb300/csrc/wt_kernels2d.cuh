@@ -4,7 +4,8 @@
 //   alpha2d             alpha_s per direction and the 2D CFL quantity (warp-shuffle maxima)
 //   stage2d             fused RHS + RK stage: a TX x TY tile plus its 3-cell halo staged row by
 //                       row with bulk copies, the x sweep then the y sweep in shared memory,
-//                       one output write per cell
+//                       one output write per cell; 104 KB of shared memory, so that two
+//                       CTAs (16 warps) share an SM
 #pragma once
 
 #include "wt_device.cuh"
@@ -22,22 +23,23 @@ struct Tile2D {
   static constexpr int NIY = TX * (TY + 1);      // y-interfaces
   static constexpr int NI = NIX > NIY ? NIX : NIY;
   static constexpr int NT = 256;
+  static_assert(TX * TY <= NT, "one cell per thread in the flux difference and the stage update");
+  // Buffers are reused across the sweeps: the physical flux buffer holds f for the x sweep,
+  // then g for the y sweep; the reconstruction buffer holds F, then h of the same sweep; the
+  // x sweep's flux difference stays in registers until the update; the eigenvector buffer
+  // takes the block reductions at the end.
   static constexpr int kBar = 0;
   static constexpr int kUin = 2;                       // [4][RY][WX]
-  static constexpr int kUn = kUin + 4 * NCELL;         // [4][TY][WX] (interior rows)
-  static constexpr int kU = kUn + 4 * TY * WX;         // velocity u per staged cell
+  static constexpr int kU = kUin + 4 * NCELL;          // velocity u per staged cell
   static constexpr int kV = kU + NCELL;
   static constexpr int kH = kV + NCELL;
   static constexpr int kSr = kH + NCELL;
-  static constexpr int kFx = kSr + NCELL;              // [4][NCELL] f
-  static constexpr int kFy = kFx + 4 * NCELL;          // [4][NCELL] g
-  static constexpr int kL = kFy + 4 * NCELL;           // [16][NI]
+  static constexpr int kFg = kSr + NCELL;              // [4][NCELL] f, then g
+  static constexpr int kL = kFg + 4 * NCELL;           // [16][NI]; 8 * 32 + 32 for the reductions
   static constexpr int kRs = kL + 16 * NI;             // [4][NI]
-  static constexpr int kF = kRs + 4 * NI;              // [4][NI]
-  static constexpr int kHf = kF + 4 * NI;              // [4][NI]
-  static constexpr int kLx = kHf + 4 * NI;             // [4][TY][TX]
-  static constexpr int kRed = kLx + 4 * TX * TY;       // 8 * 32 + 32
-  static constexpr int kTotal = kRed + 9 * 32;
+  static constexpr int kF = kRs + 4 * NI;              // [4][NI] F, then h
+  static constexpr int kTotal = kF + 4 * NI;
+  static_assert(16 * NI >= 9 * 32, "reduction scratch inside the eigenvector buffer");
   static constexpr size_t bytes = sizeof(double) * kTotal;
 };
 
@@ -76,25 +78,22 @@ __global__ void __launch_bounds__(256) alpha2d_kernel(const double* __restrict__
 }
 
 template <class MATH, int STAGE, int TX, int TY>
-__global__ void __launch_bounds__(Tile2D<TX, TY>::NT) stage2d_kernel(const Stage2DArgs a) {
+__global__ void __launch_bounds__(Tile2D<TX, TY>::NT, 2) stage2d_kernel(const Stage2DArgs a) {
   using TL = Tile2D<TX, TY>;
   constexpr int WX = TL::WX, RY = TL::RY, NCELL = TL::NCELL, NI = TL::NI, NT = TL::NT;
   extern __shared__ __align__(16) double sm[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + TL::kBar);
   double* s_uin = sm + TL::kUin;
-  double* s_un = sm + TL::kUn;
   double* s_u = sm + TL::kU;
   double* s_v = sm + TL::kV;
   double* s_H = sm + TL::kH;
   double* s_sr = sm + TL::kSr;
-  double* s_fx = sm + TL::kFx;
-  double* s_fy = sm + TL::kFy;
+  double* s_fg = sm + TL::kFg;
   double* s_L = sm + TL::kL;
   double* s_rs = sm + TL::kRs;
   double* s_F = sm + TL::kF;
-  double* s_h = sm + TL::kHf;
-  double* s_Lx = sm + TL::kLx;
-  double* s_red = sm + TL::kRed;
+  double* s_h = s_F;
+  double* s_red = s_L;
 
   pdl_launch_dependents();
   pdl_wait();
@@ -140,7 +139,8 @@ __global__ void __launch_bounds__(Tile2D<TX, TY>::NT) stage2d_kernel(const Stage
     dt = ctl->dt;
   }
 
-  // ---- A: stage rows y0-3 .. y0+tcy+2, columns x0-3 .. x0+tcx+2 of every plane
+  // ---- A: stage rows y0-3 .. y0+tcy+2, columns x0-3 .. x0+tcx+2 of every plane (u^n of
+  //      stages 2 and 3 is read in phase E, one load per cell)
   const int rows = tcy + 2 * G;
   const int len = (tcx + 2 * G + 1) & ~1;
   constexpr bool kNeedUn = (STAGE == STAGE_RK2 || STAGE == STAGE_RK3);
@@ -148,18 +148,12 @@ __global__ void __launch_bounds__(Tile2D<TX, TY>::NT) stage2d_kernel(const Stage
   __syncthreads();
   if (tid < 32) {
     const uint32_t bytes = (uint32_t)len * 8u;
-    const int ncopy = 4 * rows + (kNeedUn ? 4 * tcy : 0);
+    const int ncopy = 4 * rows;
     if (tid == 0) mbar_arrive_expect_tx(bar, bytes * (uint32_t)ncopy);
     __syncwarp();
     for (int k = tid; k < ncopy; k += 32) {
-      if (k < 4 * rows) {
-        const int c = k / rows, r = k - c * rows;
-        bulk_g2s(s_uin + (c * RY + r) * WX, a.uin + c * a.planep + (y0 + r) * a.rowp + x0, bytes, bar);
-      } else {
-        const int kk = k - 4 * rows;
-        const int c = kk / tcy, r = kk - c * tcy;
-        bulk_g2s(s_un + (c * TY + r) * WX, a.un + c * a.planep + (y0 + G + r) * a.rowp + x0, bytes, bar);
-      }
+      const int c = k / rows, r = k - c * rows;
+      bulk_g2s(s_uin + (c * RY + r) * WX, a.uin + c * a.planep + (y0 + r) * a.rowp + x0, bytes, bar);
     }
   }
   const bool ok = mbar_wait_bounded(bar, 0);
@@ -169,7 +163,8 @@ __global__ void __launch_bounds__(Tile2D<TX, TY>::NT) stage2d_kernel(const Stage
     return;
   }
 
-  // ---- B: per staged cell of the cross (interior rows with x-halo, interior columns with y-halo)
+  // ---- B: per staged cell of the cross (interior rows with x-halo, interior columns with
+  //      y-halo): velocities, H, sqrt(rho) and f; g follows once the x sweep is done with f
   for (int k = tid; k < NCELL; k += NT) {
     const int r = k / WX, col = k - r * WX;
     if (r >= rows || col >= tcx + 2 * G) continue;
@@ -183,10 +178,9 @@ __global__ void __launch_bounds__(Tile2D<TX, TY>::NT) stage2d_kernel(const Stage
     s_v[k] = v;
     s_H[k] = H;
     s_sr[k] = sr;
+    if (yin) {
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      s_fx[c * NCELL + k] = f[c];
-      s_fy[c * NCELL + k] = g[c];
+      for (int c = 0; c < 4; ++c) s_fg[c * NCELL + k] = f[c];
     }
   }
   __syncthreads();
@@ -214,7 +208,7 @@ __global__ void __launch_bounds__(Tile2D<TX, TY>::NT) stage2d_kernel(const Stage
 #pragma unroll
     for (int kk = 0; kk < 6; ++kk) {
       const int k = (r + G) * WX + i + kk;
-      const double f[4] = {s_fx[k], s_fx[NCELL + k], s_fx[2 * NCELL + k], s_fx[3 * NCELL + k]};
+      const double f[4] = {s_fg[k], s_fg[NCELL + k], s_fg[2 * NCELL + k], s_fg[3 * NCELL + k]};
       const double U[4] = {s_uin[k], s_uin[NCELL + k], s_uin[2 * NCELL + k], s_uin[3 * NCELL + k]};
       MATH::project4(0, l, f, U, al, vp[kk], vm[kk]);
     }
@@ -224,6 +218,8 @@ __global__ void __launch_bounds__(Tile2D<TX, TY>::NT) stage2d_kernel(const Stage
     s_F[s * NI + it] = MATH::weno(vp, a.eps, a.alpha_R) + MATH::weno(qm, a.eps, a.alpha_R);
   }
   __syncthreads();
+  // back-projection in place (F -> h of the same interface), and g of the y-sweep cells into
+  // the flux buffer, which the x sweep no longer reads
   for (int it = tid; it < nix; it += NT) {
     const double rs[4] = {s_rs[it], s_rs[NI + it], s_rs[2 * NI + it], s_rs[3 * NI + it]};
     const double F[4] = {s_F[it], s_F[NI + it], s_F[2 * NI + it], s_F[3 * NI + it]};
@@ -232,14 +228,24 @@ __global__ void __launch_bounds__(Tile2D<TX, TY>::NT) stage2d_kernel(const Stage
 #pragma unroll
     for (int c = 0; c < 4; ++c) s_h[c * NI + it] = h[c];
   }
-  __syncthreads();
-  for (int k = tid; k < tcx * tcy; k += NT) {
-    const int r = k / tcx, t = k - r * tcx;
-    const int it = r * (tcx + 1) + t;
+  for (int q = tid; q < rows * tcx; q += NT) {
+    const int r = q / tcx, k = r * WX + G + (q - r * tcx);
+    const double U[4] = {s_uin[k], s_uin[NCELL + k], s_uin[2 * NCELL + k], s_uin[3 * NCELL + k]};
+    double g[4];
+    MATH::euler2d_gflux(U, s_u[k], s_v[k], a.gamma, g);
 #pragma unroll
-    for (int c = 0; c < 4; ++c) s_Lx[c * TX * TY + r * TX + t] = MATH::flux_diff(s_h[c * NI + it + 1], s_h[c * NI + it], a.dx, a.inv_dx);
+    for (int c = 0; c < 4; ++c) s_fg[c * NCELL + k] = g[c];
   }
   __syncthreads();
+  // the x sweep's flux difference of this thread's cell (the cell of phase E), and the y
+  // sweep's Roe averages
+  double Lx[4] = {0.0, 0.0, 0.0, 0.0};
+  if (tid < tcx * tcy) {
+    const int r = tid / tcx, t = tid - r * tcx;
+    const int it = r * (tcx + 1) + t;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) Lx[c] = MATH::flux_diff(s_h[c * NI + it + 1], s_h[c * NI + it], a.dx, a.inv_dx);
+  }
 
   // ---- y sweep.  Interface j of column t sits between cells (j+2, t+3) and (j+3, t+3).
   const int niy = tcx * (tcy + 1);
@@ -264,7 +270,7 @@ __global__ void __launch_bounds__(Tile2D<TX, TY>::NT) stage2d_kernel(const Stage
 #pragma unroll
     for (int kk = 0; kk < 6; ++kk) {
       const int k = (j + kk) * WX + t + G;
-      const double f[4] = {s_fy[k], s_fy[NCELL + k], s_fy[2 * NCELL + k], s_fy[3 * NCELL + k]};
+      const double f[4] = {s_fg[k], s_fg[NCELL + k], s_fg[2 * NCELL + k], s_fg[3 * NCELL + k]};
       const double U[4] = {s_uin[k], s_uin[NCELL + k], s_uin[2 * NCELL + k], s_uin[3 * NCELL + k]};
       MATH::project4(1, l, f, U, al, vp[kk], vm[kk]);
     }
@@ -288,22 +294,25 @@ __global__ void __launch_bounds__(Tile2D<TX, TY>::NT) stage2d_kernel(const Stage
   unsigned long long vmax[8], qmax = 0ull;
 #pragma unroll
   for (int s = 0; s < 8; ++s) vmax[s] = 0ull;
-  for (int k = tid; k < tcx * tcy; k += NT) {
-    const int r = k / tcx, t = k - r * tcx;
+  if (tid < tcx * tcy) {
+    const int r = tid / tcx, t = tid - r * tcx;
     const long long x = x0 + t, y = y0 + r;
     const int kc = (r + G) * WX + t + G;
+    double un4[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) un4[c] = kNeedUn ? a.un[c * a.planep + (y + G) * a.rowp + x + G] : 0.0;
     double uo[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       const double Ly = MATH::flux_diff(s_h[c * NI + (r + 1) * tcx + t], s_h[c * NI + r * tcx + t], a.dy, a.inv_dy);
-      double L = MATH::add_sweeps(s_Lx[c * TX * TY + r * TX + t], Ly);
+      double L = MATH::add_sweeps(Lx[c], Ly);
       // gravity along -y (TEST 6, Sec. 4.3): -g rho on the y momentum, -g rho v on the energy
       if (c >= 2 && a.gravity != 0.0) L = MATH::add_source(L, a.gravity, s_uin[(c == 2 ? 0 : 2) * NCELL + kc]);
       if (STAGE == STAGE_RHS) {
         a.Lout[(c * ny + y) * nx + x] = L;
       } else {
         const double us = s_uin[c * NCELL + kc];
-        const double un = kNeedUn ? s_un[(c * TY + r) * WX + t + G] : us;
+        const double un = kNeedUn ? un4[c] : us;
         uo[c] = MATH::template rk<(STAGE == STAGE_RHS ? 0 : STAGE)>(un, us, dt, L);
       }
     }
@@ -375,10 +384,16 @@ cudaError_t prepare_stage2d_policy() {
   constexpr int TX = 32, TY = 8;
   using TL = Tile2D<TX, TY>;
   cudaError_t e = cudaSuccess;
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(stage2d_kernel<MATH, STAGE_RK1, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TL::bytes);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(stage2d_kernel<MATH, STAGE_RK2, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TL::bytes);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(stage2d_kernel<MATH, STAGE_RK3, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TL::bytes);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(stage2d_kernel<MATH, STAGE_RHS, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TL::bytes);
+  // the tile's shared memory, and the largest carveout, so that two CTAs fit on an SM
+  const void* kerns[4] = {(const void*)stage2d_kernel<MATH, STAGE_RK1, TX, TY>,
+                          (const void*)stage2d_kernel<MATH, STAGE_RK2, TX, TY>,
+                          (const void*)stage2d_kernel<MATH, STAGE_RK3, TX, TY>,
+                          (const void*)stage2d_kernel<MATH, STAGE_RHS, TX, TY>};
+  for (int i = 0; i < 4 && e == cudaSuccess; ++i) {
+    e = cudaFuncSetAttribute(kerns[i], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TL::bytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(kerns[i], cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  }
   return e;
 }
 

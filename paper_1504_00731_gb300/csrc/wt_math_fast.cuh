@@ -457,8 +457,8 @@ struct FastMath {
     const double ir = 1.0 / U[0];
     u = U[1] * ir;
     v = U[2] * ir;
-    const double p = (gamma - 1.0) * fma(-0.5, dot2(U[1], u, U[2], v), U[3]);
-    const double e = U[3] + p;
+    const double p = __dmul_rn(gamma - 1.0, fma(-0.5, dot2(U[1], u, U[2], v), U[3]));
+    const double e = __dadd_rn(U[3], p);
     f[0] = U[1];
     f[1] = fma(U[1], u, p);
     f[2] = U[1] * v;
@@ -469,6 +469,16 @@ struct FastMath {
     g[3] = e * v;
     H = e * ir;
     sr = sqrt(U[0]);
+  }
+  // g of euler2d_cell alone, from the u and v it returned (the same operations; p and e are
+  // rounded explicitly in both, so that neither is contracted differently at either site)
+  __device__ __forceinline__ static void euler2d_gflux(const double* U, double u, double v, double gamma, double* g) {
+    const double p = __dmul_rn(gamma - 1.0, fma(-0.5, dot2(U[1], u, U[2], v), U[3]));
+    const double e = __dadd_rn(U[3], p);
+    g[0] = U[2];
+    g[1] = U[2] * u;  // rho v u, computed as the transpose of f[2]
+    g[2] = fma(U[2], v, p);
+    g[3] = e * v;
   }
 
   __device__ __forceinline__ static void euler2d_speeds(const double* U, double gamma, double dx, double dy,

@@ -240,6 +240,14 @@ struct StrictMath {
     H = (U[3] + p) / U[0];
     sr = sqrt(U[0]);
   }
+  // g of euler2d_cell alone, from the u and v it returned (the same operations)
+  __device__ __forceinline__ static void euler2d_gflux(const double* U, double u, double v, double gamma, double* g) {
+    const double p = (gamma - 1.0) * (U[3] - 0.5 * U[0] * (u * u + v * v));
+    g[0] = U[2];
+    g[1] = U[2] * u;
+    g[2] = p + U[2] * v;
+    g[3] = (U[3] + p) * v;
+  }
 
   // |lambda| in x (u-c, u, u, u+c) and y (v-c, v, v, v+c) and the CFL quantity
   // (|u| + c)/dx + (|v| + c)/dy
