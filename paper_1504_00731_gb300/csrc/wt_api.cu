@@ -34,6 +34,8 @@ int fail(int code, const char* fmt, ...) {
   } while (0)
 
 constexpr size_t kAlign = 256;
+// the step-blocked kernel reads each CTA's alpha words as one aligned 32-byte record
+static_assert(kAlign % 32 == 0, "workspace regions must start 32-byte aligned");
 inline size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
 int expected_m(int flux) {

@@ -41,6 +41,8 @@ struct Tile2D {
   static constexpr int kTotal = kF + 4 * NI;
   static_assert(16 * NI >= 9 * 32, "reduction scratch inside the eigenvector buffer");
   static constexpr size_t bytes = sizeof(double) * kTotal;
+  // two CTAs per SM: 228 KB of shared memory per SM, 1 KB of it reserved per CTA
+  static_assert(2 * (bytes + 1024) <= 228 * 1024, "two tiles must fit on one SM");
 };
 
 __global__ void pack2d_kernel(const double* __restrict__ src, double* __restrict__ dst, long long nx, long long ny,
