@@ -185,6 +185,45 @@ def test_quadratic_exactness(oracle):
             assert np.max(np.abs(L[0, sl] - exact[sl])) < 1e-11 * max(1, np.abs(exact).max())
 
 
+def test_polynomial_exactness_of_the_linear_schemes(oracle):
+    """Where a stencil is restricted, Eq. (fh_we6) is the linear scheme of Eq. (fh_5) (theta = 1)
+    or Eq. (fh_6) (theta = 0).  The finite-difference flux of Eq. (mod_semi) then gives
+    L_j = -p'(x_j) exactly for a polynomial flux p of degree 5 with either scheme, and of
+    degree 6 only with the central one: the interface value is exact to degree 4 (upwind) or
+    5 (central), and the next error term has a constant coefficient that cancels in the
+    difference.  Linear advection, a = 1, so the split flux of the plus side is u and the
+    other side is zero; the decisions per interface come from the oracle's reconstruction.
+    Coefficients grow with the degree on a coarse grid, so that theta = 1 occurs too."""
+    O = oracle
+    rng = np.random.default_rng(12)
+    n = 24
+    x, dx = W.grid_1d(n, -1.0, 1.0, periodic=False)
+    seen = {5: {0: 0, 1: 0}, 6: {0: 0, 1: 0}}
+    for deg in (5, 6):
+        for trial in range(20):
+            c = rng.uniform(-1, 1, deg + 1)
+            c[deg] = rng.choice([-1.0, 1.0]) * rng.uniform(0.5, 1.0)
+            c = c * rng.uniform(0.2, 5.0, deg + 1) ** np.arange(deg + 1)
+            u = np.polyval(c[::-1], x)[None, :]
+            dp = np.polyval(np.polyder(c[::-1]), x)
+            L = O.rhs(O.problem(O.FLUX_ADVECTION, alpha_R=50.0, bc=O.BC_OUTFLOW), u, dx)[0]
+            scale = np.abs(u).max() / dx
+            for j in range(3, n - 3):
+                right = O.weno_theta(u[0, j - 2:j + 4], 1e-10, 50.0)
+                left = O.weno_theta(u[0, j - 3:j + 3], 1e-10, 50.0)
+                if not (right[2] and left[2]) or right[1] != left[1]:
+                    continue  # a nonlinear weight, or the two schemes mixed
+                theta = right[1]
+                err = abs(L[j] + dp[j])
+                if deg == 5 or theta == 0:
+                    assert err <= 1e-13 * scale, (deg, j, theta, err / scale)
+                else:
+                    # the upwind scheme's error ~ p^(6) dx^5: far above rounding (~1e-16)
+                    assert err > 1e-11 * scale, (deg, j, err / scale)
+                seen[deg][theta] += 1
+    assert seen[5][0] > 100 and seen[6][0] > 100 and seen[5][1] >= 2 and seen[6][1] >= 3, seen
+
+
 def test_smooth_convergence_order(oracle):
     """6th order on smooth periodic data (Sec. 3.2): seeded three-mode advection and an Euler
     entropy wave (exact solution: translation), dt = dx^2 so space dominates."""
