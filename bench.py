@@ -329,17 +329,23 @@ def adjoint_measure(B, dev, nprob=256, n=16384, steps=64, K=32, K_full=2):
 
 
 def problems_measure(B, dev):
-    """The test problems of Sec. 4.2 / 4.3 built on reflective walls and gravity: two
-    interacting blast waves (TEST 5, N = 801, alpha_R = 10, the paper's run to t = 0.038), the
-    Rayleigh-Taylor instability (TEST 6, 120 x 360, gravity 0.1, 2000 of the ~17600 steps to
-    t = 9.5) and the implosion problem (TEST 7, 400 x 400, alpha_R = 1, 1000 of the ~16200
-    steps to t = 5); fast mode, CFL 0.5, cell-updates/s through weno_theta_step."""
+    """The small scalar workload (linear advection of sin(pi x), N = 200, periodic, CFL 0.4 to
+    t = 2: 500 steps; latency-bound) and the test problems of Sec. 4.2 / 4.3 built on
+    reflective walls and gravity: two interacting blast waves (TEST 5, N = 801, alpha_R = 10,
+    the paper's run to t = 0.038), the Rayleigh-Taylor instability (TEST 6, 120 x 360,
+    gravity 0.1, 2000 of the ~17600 steps to t = 9.5) and the implosion problem (TEST 7,
+    400 x 400, alpha_R = 1, 1000 of the ~16200 steps to t = 5); fast mode, CFL 0.5 unless
+    stated, cell-updates/s through weno_theta_step."""
     import torch
 
     stream = torch.cuda.current_stream(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     out = {}
     cases = []
+    U, x, dx = W.advection_sine(200)
+    cases.append(("advection_sine_N200_cfl0.4_t2", U, B.problem(B.WT_FLUX_ADVECTION, bc=B.WT_BC_PERIODIC,
+                                                                mode=B.WT_MODE_FAST), B.grid_1d(200, -1.0, 1.0),
+                  dict(t_final=2.0, cfl=0.4)))
     U, x, dx = W.blast_waves(801)
     cases.append(("blast_waves_N801_t0.038", U, B.problem(B.WT_FLUX_EULER1D, bc=B.WT_BC_REFLECTIVE, mode=B.WT_MODE_FAST,
                                                           alpha_R=10.0), B.grid_1d(801, 0.0, 1.0),
@@ -354,14 +360,16 @@ def problems_measure(B, dev):
                   B.problem(B.WT_FLUX_EULER2D, bc=B.WT_BC_REFLECTIVE, bc_y=B.WT_BC_REFLECTIVE, mode=B.WT_MODE_FAST,
                             alpha_R=1.0), B.grid_2d(400, 400), dict(max_steps=1000)))
     for name, U, prob, grid, kw in cases:
+        kw = dict(kw)
+        cfl = kw.pop("cfl", 0.5)
         ws = B.alloc_workspace(B.workspace_bytes(prob, grid), dev)
         u0 = torch.from_numpy(np.ascontiguousarray(U)).to(dev)
         u = u0.clone()
-        B.weno_theta_step(prob, grid, u, 0.5, ws, max_steps=3)
+        B.weno_theta_step(prob, grid, u, cfl, ws, max_steps=3)
         u.copy_(u0)
         torch.cuda.synchronize()
         e0.record(stream)
-        t, steps = B.weno_theta_step(prob, grid, u, 0.5, ws, **kw)
+        t, steps = B.weno_theta_step(prob, grid, u, cfl, ws, **kw)
         e1.record(stream)
         torch.cuda.synchronize()
         sec = e0.elapsed_time(e1) * 1e-3
