@@ -63,30 +63,73 @@ def problem(flux, gamma=1.4, adv_speed=1.0, eps=1e-10, alpha_R=50.0, bc=BC_PERIO
     return p
 
 
+def _compile(out: str, defines=()) -> None:
+    """g++ -O2 -ffp-contract=off, with OpenMP over independent problems where the compiler has it
+    (the per-problem arithmetic is the same either way)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    tmp = out + f".tmp{os.getpid()}"
+    base = ["g++", "-O2", "-ffp-contract=off", "-std=c++17", "-fPIC", "-shared"] + [f"-D{d}" for d in defines]
+    try:
+        subprocess.run(base + ["-fopenmp", "-o", tmp, _SRC], check=True, capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base + ["-o", tmp, _SRC], check=True)
+    os.replace(tmp, out)
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle shared library (host compiler only) and return its path."""
     with _lock:
         fresh = os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(_SRC)
         if fresh and not force:
             return _SO
-        os.makedirs(_BUILD, exist_ok=True)
-        tmp = _SO + f".tmp{os.getpid()}"
-        cmd = ["g++", "-O2", "-ffp-contract=off", "-std=c++17", "-fPIC", "-shared", "-o", tmp, _SRC]
-        subprocess.run(cmd, check=True)
-        os.replace(tmp, _SO)
+        _compile(_SO)
         return _SO
+
+
+def _load(path, rebuild):
+    try:
+        return ctypes.CDLL(path)
+    except OSError:  # stale library from another architecture
+        rebuild()
+        return ctypes.CDLL(path)
+
+
+def planted(name: str):
+    """The oracle built with one deliberately wrong line (``-DWTO_PLANT_<name>``), for tests that
+    show a pin fails when the oracle is wrong.  Use it with ``using(...)``."""
+    path = os.path.join(_BUILD, f"libweno_theta_oracle_plant_{name.lower()}.so")
+    with _lock:
+        if not (os.path.exists(path) and os.path.getmtime(path) >= os.path.getmtime(_SRC)):
+            _compile(path, (f"WTO_PLANT_{name}",))
+    return _declare(_load(path, lambda: _compile(path, (f"WTO_PLANT_{name}",))))
+
+
+class using:
+    """Context manager: the module's functions call ``library`` instead of the oracle."""
+
+    def __init__(self, library):
+        self.library = library
+
+    def __enter__(self):
+        global _lib
+        self.saved = lib()
+        _lib = self.library
+        return self.library
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self.saved
 
 
 def lib():
     global _lib
     if _lib is not None:
         return _lib
-    path = build()
-    try:
-        L = ctypes.CDLL(path)
-    except OSError:  # stale library from another architecture
-        path = build(force=True)
-        L = ctypes.CDLL(path)
+    _lib = _declare(_load(build(), lambda: build(force=True)))
+    return _lib
+
+
+def _declare(L):
     D = ctypes.c_double
     P = ctypes.POINTER(ctypes.c_double)
     I64 = ctypes.c_int64
@@ -107,7 +150,8 @@ def lib():
     L.wto_count_run_ops.argtypes = [PP, I64, I64, D, D, P, D, I64, PI64]
     L.wto_riemann_star.argtypes = [D, D, D, D, D, D, D, P, P, PI32]
     L.wto_riemann_sample.argtypes = [D, D, D, D, D, D, D, D, D, P, I64, P, P, P]
-    _lib = L
+    L.wto_run_batch.argtypes = [PP, ctypes.c_int32, PI64, PI64, P, P, PI32, P, I64, D, I64, ctypes.c_int32, PI64]
+    L.wto_max_threads.restype = ctypes.c_int32
     return L
 
 
@@ -253,3 +297,29 @@ def riemann_sample(left, right, x, x0, t, gamma=1.4):
     p = np.zeros_like(x)
     lib().wto_riemann_sample(*left, *right, gamma, x0, t, _ptr(x), x.size, _ptr(rho), _ptr(u), _ptr(p))
     return rho, u, p
+
+
+def max_threads():
+    """Threads ``run_batch`` uses with ``threads=0`` (1 when built without OpenMP)."""
+    return int(lib().wto_max_threads())
+
+
+def run_batch(prob, u_packed, offsets, lengths, lo, hi, bc, cfl=0.5, n_steps=1, threads=0):
+    """``n_steps`` TVD-RK3 steps of independent 1D problems in packed planes ``(m, total)``
+    (problem p at columns ``offsets[p] .. offsets[p] + lengths[p]``, grid ``[lo[p], hi[p]]``,
+    boundary ``bc[p]`` at both ends); each problem is ``run`` on its own, several at once on
+    ``threads`` threads (0: all).  Returns (u_packed_final, steps per problem)."""
+    u = np.ascontiguousarray(u_packed, dtype=np.float64).copy()
+    m, total = u.shape
+    nprob = len(lengths)
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    ln = np.ascontiguousarray(lengths, dtype=np.int64)
+    lo = np.ascontiguousarray(np.broadcast_to(lo, (nprob,)), dtype=np.float64)
+    hi = np.ascontiguousarray(np.broadcast_to(hi, (nprob,)), dtype=np.float64)
+    bc = np.ascontiguousarray(bc, dtype=np.int32)
+    steps = np.zeros(nprob, dtype=np.int64)
+    I64P = ctypes.POINTER(ctypes.c_int64)
+    lib().wto_run_batch(ctypes.byref(prob), nprob, off.ctypes.data_as(I64P), ln.ctypes.data_as(I64P), _ptr(lo),
+                        _ptr(hi), bc.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _ptr(u), total, cfl, n_steps,
+                        threads, steps.ctypes.data_as(I64P))
+    return u, steps

@@ -30,15 +30,26 @@
  * balance), exact translation (resolution test, composite wave), the characteristic
  * solution of Burgers' equation away from its shock, and the exact Riemann solution
  * (itself pinned by its pressure-function residual, the Rankine-Hugoniot relations and
- * the Riemann invariants) for Sod, Lax, 123 and the early blast waves.  Parity unpinned:
+ * the Riemann invariants) for Sod, Lax, 123 and the early blast waves.  Reflective walls
+ * (tests/test_oracle_walls.py): a uniform flow between two walls against the exact Riemann
+ * solutions of the mirrored states, conservation of mass and energy on data mirrored about
+ * the middle, 2D lines across a wall equal to the 1D run; a build with the normal momentum's
+ * sign planted wrong fails all three.  The Lax-Friedrichs constants and the CFL step against
+ * the eigenvalues of complex-step flux Jacobians, and advection with a = -2 against the
+ * closed form of the linear limit.  The sampled RHS equals the whole RHS cell by cell.
+ * Parity unpinned:
  * the solution near discontinuities beyond those monotonicity and convergence bounds
  * (Shu-Osher only by self-convergence), and the value alpha_R = 10 on the seeded Euler
  * workloads (a convention; the paper sets alpha_R per test).
  */
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 namespace wto {
 
@@ -369,6 +380,11 @@ struct Line {
  * Reflective: mirror image with the normal momentum negated. */
 template <class R>
 void fill_ghosts(Line<R>& L, int bc_lo, int bc_hi, int normal_comp) {
+#ifdef WTO_PLANT_REFLECT_SIGN
+  /* A deliberately wrong variant, built only by a test that must see its pins fail: the
+   * reflective ghost keeps the sign of the normal momentum. */
+  normal_comp = -1;
+#endif
   for (int c = 0; c < L.m; ++c) {
     for (int k = 1; k <= G; ++k) {
       R lo, hi;
@@ -882,6 +898,48 @@ void wto_count_run_ops(const Problem* P, int64_t nx, int64_t ny, double dx, doub
   out[2] = g_ops.div;
   out[3] = g_ops.sqrt;
   out[4] = g_ops.cmp;
+}
+
+/* Time integration of nprob independent 1D problems stored in packed planes
+ * u[c * total + offsets[p] + j] (j < lengths[p]), each on its own grid [lo[p], hi[p]] with
+ * boundary condition bc[p] at both ends, n_steps steps each with its own CFL step (t_final =
+ * +inf).  Every problem is the serial run() above on its own copy of the data, so the result
+ * does not depend on how many threads share the problems (OpenMP over problems, largest
+ * first, when the library is built with -fopenmp).  steps_out[p] (may be NULL): steps taken. */
+void wto_run_batch(const Problem* P, int32_t nprob, const int64_t* offsets, const int64_t* lengths, const double* lo,
+                   const double* hi, const int32_t* bc, double* u, int64_t total, double cfl, int64_t n_steps,
+                   int32_t nthreads, int64_t* steps_out) {
+  std::vector<int32_t> order((size_t)nprob);
+  for (int32_t p = 0; p < nprob; ++p) order[(size_t)p] = p;
+  std::sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return lengths[a] > lengths[b]; });
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+  for (int32_t k = 0; k < nprob; ++k) {
+    const int32_t p = order[(size_t)k];
+    const int64_t n = lengths[p];
+    Problem Q = *P;
+    Q.bc_lo[0] = Q.bc_hi[0] = bc[p];
+    Grid g{n, 1, (hi[p] - lo[p]) / (double)n, 1.0};
+    std::vector<double> w((size_t)Q.m * n);
+    for (int c = 0; c < Q.m; ++c)
+      for (int64_t j = 0; j < n; ++j) w[(size_t)c * n + j] = u[(size_t)c * total + offsets[p] + j];
+    int64_t steps = 0;
+    run(Q, g, w.data(), cfl, 0.0, INFINITY, n_steps, (double*)0, &steps);
+    for (int c = 0; c < Q.m; ++c)
+      for (int64_t j = 0; j < n; ++j) u[(size_t)c * total + offsets[p] + j] = w[(size_t)c * n + j];
+    if (steps_out) steps_out[p] = steps;
+  }
+}
+
+/* Threads wto_run_batch uses when nthreads = 0 (1 without OpenMP). */
+int32_t wto_max_threads(void) {
+#ifdef _OPENMP
+  return (int32_t)omp_get_max_threads();
+#else
+  return 1;
+#endif
 }
 
 /* Exact Riemann problem: star state and the solution sampled at xs (jump at x0, time t). */

@@ -177,30 +177,37 @@ def batch_lengths(nprob: int, seed: int, nmin=256, nmax=65536):
     return np.rint(np.exp(rng.uniform(math.log(nmin), math.log(nmax), nprob))).astype(np.int64)
 
 
-def euler_batch(nprob: int, seed: int, nmin=256, nmax=65536, lengths=None, amp_scale=None):
+def euler_batch(nprob: int, seed: int, nmin=256, nmax=65536, lengths=None, amp_scale=None, problems=None):
     """Seeded batch: lengths log-uniform in [nmin, nmax], boundary periodic or outflow by coin flip,
-    Riemann + entropy-wave data with per-problem seeds (seed * 1_000_003 + p)."""
+    Riemann + entropy-wave data with per-problem seeds (seed * 1_000_003 + p).
+
+    ``problems`` (indices into the nprob problems of the seed, default all) builds only those
+    problems, packed in the given order: one rank's share of a partitioned batch.  The draws
+    are prefix-stable, so the first k problems of a larger batch are those of a k-problem one."""
     if lengths is None:
         lengths = batch_lengths(nprob, seed, nmin, nmax)
     lengths = np.asarray(lengths, dtype=np.int64)
     rng = np.random.default_rng(seed + 7)
     bc = rng.integers(0, 2, nprob).astype(np.int32)
-    offsets = np.zeros(nprob, dtype=np.int64)
+    ids = np.arange(nprob) if problems is None else np.asarray(problems, dtype=np.int64)
+    lengths, bc = lengths[ids], bc[ids]
+    k = len(ids)
+    offsets = np.zeros(k, dtype=np.int64)
     offsets[1:] = np.cumsum(lengths)[:-1]
     u = np.empty((3, int(lengths.sum())))
-    dx = np.empty(nprob)
+    dx = np.empty(k)
     params = []
-    for p in range(nprob):
-        prm = riemann_params(seed * 1_000_003 + p)
+    for i, p in enumerate(ids):
+        prm = riemann_params(seed * 1_000_003 + int(p))
         if amp_scale is not None:
             s = amp_scale[p]
             prm = RiemannParams(prm.rhoL * s[0], prm.uL, prm.pL * s[1], prm.rhoR * s[2], prm.uR, prm.pR * s[3],
                                 prm.x0, prm.k, prm.amp * s[4])
-        U, x, d = euler_riemann(int(lengths[p]), prm, periodic=bool(bc[p] == 0))
-        u[:, offsets[p]:offsets[p] + lengths[p]] = U
-        dx[p] = d
+        U, x, d = euler_riemann(int(lengths[i]), prm, periodic=bool(bc[i] == 0))
+        u[:, offsets[i]:offsets[i] + lengths[i]] = U
+        dx[i] = d
         params.append(prm)
-    return Batch(lengths, offsets, bc, dx, np.full(nprob, -5.0), np.full(nprob, 5.0), u, params)
+    return Batch(lengths, offsets, bc, dx, np.full(k, -5.0), np.full(k, 5.0), u, params)
 
 
 def amplitude_perturbation(nprob: int, seed: int, rel=0.01):

@@ -330,16 +330,74 @@ def test_roe_matrix_property(oracle):
             assert np.max(np.abs(A @ (Ub2 - Ua2) - df)) < 1e-12 * max(1, np.abs(df).max())
 
 
+def _jacobian_spectrum(flux, U, eps=1e-30):
+    """Eigenvalues (sorted) of df/du at U by complex-step differentiation of the test's own flux:
+    exact to rounding, and independent of the oracle's eigenvalue formulas."""
+    m = U.shape[0]
+    J = np.zeros((m, m))
+    for k in range(m):
+        dU = U.astype(complex)
+        dU[k] += 1j * eps
+        J[:, k] = np.imag(flux(dU)) / eps
+    return np.sort(np.linalg.eigvals(J).real)
+
+
 def test_alpha_and_cfl_step(oracle):
-    """Global Lax-Friedrichs alpha_s = max_j |lambda_s(u_j)| (Eq. (flux_split_lf)) and the CFL
-    step dt = CFL dx / max_j(|u_j| + c_j) = CFL dx / max(alpha_1, alpha_3) for Euler."""
+    """Eq. (flux_split_lf): alpha_s = max over the cells of |lambda_s|, lambda_s the s-th eigenvalue
+    of the flux Jacobian f'(u_j); the CFL step is CFL dx / max_j rho(f'(u_j)) (2D:
+    CFL / max_j (rho(f'(u_j))/dx + rho(g'(u_j))/dy)).  The spectra come from numpy's eigenvalues
+    of the complex-step Jacobian of the flux as Sec. 4.2 / 4.3 print it, not from the oracle."""
     O = oracle
     U, x, dx = W.euler_c2(512, seed=1)
-    rho, u, p = W.prim_1d(U)
-    c = np.sqrt(1.4 * p / rho)
+    lam = np.array([_jacobian_spectrum(_euler_flux_1d, U[:, j]) for j in range(U.shape[1])])
     a, dt = O.alpha(O.problem(O.FLUX_EULER1D, bc=O.BC_OUTFLOW), U, dx, cfl=0.5)
-    assert np.allclose(a[0, :3], [np.abs(u - c).max(), np.abs(u).max(), np.abs(u + c).max()], rtol=1e-15, atol=0)
-    assert dt == 0.5 * dx / max(a[0, 0], a[0, 2])
+    assert np.allclose(a[0, :3], np.abs(lam).max(axis=0), rtol=1e-12, atol=0)
+    assert dt == pytest.approx(0.5 * dx / np.abs(lam).max(), rel=1e-12)
+    # 2D: per direction, four fields (the shear wave repeats the entropy wave's speed)
+    rng = np.random.default_rng(4)
+    sh = (6, 7)
+    U2 = W.cons_2d(0.5 + rng.uniform(size=sh), rng.uniform(-1, 1, sh), rng.uniform(-1, 1, sh),
+                   0.2 + rng.uniform(size=sh))
+    cols = U2.reshape(4, -1)
+    dx2, dy2 = 0.1, 0.3
+    a2, dt2 = O.alpha(O.problem(O.FLUX_EULER2D), U2, dx2, dy2, cfl=0.45)
+    rate = 0.0
+    spec = []
+    for d in (0, 1):
+        lam2 = np.array([_jacobian_spectrum(lambda V: _euler_flux_2d(V, d), cols[:, j]) for j in range(cols.shape[1])])
+        spec.append(np.abs(lam2).max(axis=1))
+        assert np.allclose(a2[d], np.abs(lam2).max(axis=0), rtol=1e-12, atol=0)
+    rate = (spec[0] / dx2 + spec[1] / dy2).max()
+    assert dt2 == pytest.approx(0.45 / rate, rel=1e-12)
+    # Burgers: f'(u) = u
+    ub = rng.uniform(-2, 1, (1, 50))
+    ab, dtb = O.alpha(O.problem(O.FLUX_BURGERS), ub, 0.02, cfl=0.4)
+    assert ab[0, 0] == np.abs(ub).max() and dtb == pytest.approx(0.4 * 0.02 / np.abs(ub).max(), rel=1e-15)
+
+
+def test_advection_speed_sign_and_step(oracle):
+    """u_t - 2 u_x = 0 (a = -2), sin(pi x), N = 200, CFL 0.4 to t = 1: the discrete solution is the
+    closed form of the linear limit with z_n = -a dt_n g(pi dx)/dx, which the run reproduces
+    only with dt = CFL dx / |a| (500 steps) and the wave travelling left."""
+    O = oracle
+    n, a = 200, -2.0
+    u0, x, dx = W.advection_sine(n)
+    P = O.problem(O.FLUX_ADVECTION, adv_speed=a)
+    al, dt0 = O.alpha(P, u0, dx, cfl=0.4)
+    assert al[0, 0] == 2.0 and dt0 == 0.4 * dx / 2.0
+    u, t, steps = O.run(P, u0, dx, cfl=0.4, t_final=1.0)
+    g = _linear_limit_symbol(np.pi * dx)
+    amp, tt, k = 1.0 + 0j, 0.0, 0
+    while tt < 1.0:
+        dt = min(0.4 * dx / abs(a), 1.0 - tt)
+        z = -a * dt * g / dx
+        amp *= 1.0 + z + z * z / 2.0 + z ** 3 / 6.0
+        tt += dt
+        k += 1
+    assert k == steps == 500 and tt == t
+    assert np.max(np.abs(u[0] - np.imag(amp * np.exp(1j * np.pi * x)))) < 1e-12
+    # one unit of time at speed -2 is one period: back to sin(pi x) up to the RK3 amplitude loss
+    assert np.max(np.abs(u[0] - np.sin(np.pi * x))) < 1e-5
 
 
 # ---------------------------------------------------------------------------------------------
