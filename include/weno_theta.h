@@ -155,15 +155,25 @@ int weno_theta_step(const wt_problem* prob, const wt_grid* grid, double* u, doub
  * Advances nprob independent 1D problems (each its own grid, boundary conditions,
  * Lax-Friedrichs constants and CFL step) by n_steps RK3 steps in one launch per RK
  * stage over all problems.  prob->flux must be 1D (advection, Burgers or Euler 1D).
- *   segs             [nprob] host array of wt_segment; segments must not overlap
- *   u_packed         [m][total] state, host or device, updated on success;
- *                    total = max(offset + n) over the segments
- *   t_per_problem    [nprob] out (host or device, may be NULL): time reached per problem
+ * The problems share no data: each is the scheme of Eqs. (mod_semi), (fh_nonlinear),
+ * (flux_split_lf) and (3rd_RK) on its own grid, with its own alpha_s and dt.
+ *   segs               [nprob] host array of wt_segment; segments must not overlap
+ *   u_packed           [m][total] state, host or device, updated on success;
+ *                      total = max(offset + n) over the segments
+ *   t_per_problem      [nprob] out (host or device, may be NULL): time reached per problem
+ *   status_per_problem [nprob] out (host or device, may be NULL): wt_status per problem.
+ *                      NULL: the first problem whose state became non-finite (or whose
+ *                      device wait gave up) fails the whole call and u_packed is untouched.
+ *                      Non-NULL: such a problem stops at the step where it failed, its status
+ *                      (WT_ERR_NONPHYSICAL or WT_ERR_TIMEOUT) is stored here, its part of
+ *                      u_packed keeps the input state, every other problem is written back
+ *                      as without it (bit for bit), and the call returns WT_OK;
+ *                      wt_last_error() then names how many failed.
  * Synchronises `stream` before returning.
  */
 int weno_theta_step_batched(const wt_problem* prob, const wt_segment* segs, int32_t nprob, double* u_packed,
-                            int64_t total, double cfl, int64_t n_steps, double* t_per_problem, void* ws,
-                            size_t ws_bytes, void* stream);
+                            int64_t total, double cfl, int64_t n_steps, double* t_per_problem,
+                            int32_t* status_per_problem, void* ws, size_t ws_bytes, void* stream);
 
 /*
  * Gradient of J(u(T)) with respect to u(0) through n_steps RK3 steps (CFL step from u^n,

@@ -46,6 +46,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 #ifdef _OPENMP
 #include <omp.h>
@@ -572,9 +573,17 @@ void rhs(const Problem& P, const Grid& g, const R* u, R* Lout, long long* theta1
   R alpha[8];
   compute_alpha(P, g, u, alpha);
   for (int64_t j = 0; j < cells * m; ++j) Lout[j] = R(0.0);
-  std::vector<R> hF;
+  /* Rows (and columns) are independent and write disjoint entries of Lout, so with OpenMP they
+   * may run on several threads (values only: the counters and the Dual / Cnt types stay serial);
+   * every entry is computed by the same operations either way. */
+  const bool par = std::is_same<R, double>::value && !theta1 && !restricted;
+  (void)par;
   /* x sweep: every row */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) if (par && ny > 1)
+#endif
   for (int64_t r = 0; r < ny; ++r) {
+    std::vector<R> hF;
     Line<R> L(m, (int)nx);
     for (int c = 0; c < m; ++c)
       for (int64_t i = 0; i < nx; ++i) L.at(c, (int)i) = u[(size_t)c * cells + r * nx + i];
@@ -588,7 +597,11 @@ void rhs(const Problem& P, const Grid& g, const R* u, R* Lout, long long* theta1
   }
   if (ndim_of(P) == 1) return;
   /* y sweep: every column; L = Lx + Ly */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) if (par)
+#endif
   for (int64_t col = 0; col < nx; ++col) {
+    std::vector<R> hF;
     Line<R> L(m, (int)ny);
     for (int c = 0; c < m; ++c)
       for (int64_t j = 0; j < ny; ++j) L.at(c, (int)j) = u[(size_t)c * cells + j * nx + col];

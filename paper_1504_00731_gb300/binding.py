@@ -100,7 +100,7 @@ def lib():
                                   ctypes.c_int64, P(ctypes.c_double), P(ctypes.c_int64), vp, ctypes.c_size_t, vp]
     L.weno_theta_step.restype = ctypes.c_int
     L.weno_theta_step_batched.argtypes = [P(WtProblem), P(WtSegment), ctypes.c_int32, vp, ctypes.c_int64,
-                                          ctypes.c_double, ctypes.c_int64, vp, vp, ctypes.c_size_t, vp]
+                                          ctypes.c_double, ctypes.c_int64, vp, vp, vp, ctypes.c_size_t, vp]
     L.weno_theta_step_batched.restype = ctypes.c_int
     L.wt_adjoint_workspace_bytes.argtypes = [P(WtProblem), P(WtGrid), ctypes.c_int32, ctypes.c_int64, ctypes.c_int32]
     L.wt_adjoint_workspace_bytes.restype = ctypes.c_size_t
@@ -237,12 +237,16 @@ def weno_theta_step(prob, grid, u, cfl, ws, dt_fixed=0.0, t_final=float("inf"), 
     return t.value, s.value
 
 
-def weno_theta_step_batched(prob, segs, u_packed, total, cfl, n_steps, ws, t_per_problem=None, stream=None):
+def weno_theta_step_batched(prob, segs, u_packed, total, cfl, n_steps, ws, t_per_problem=None, stream=None,
+                            status_per_problem=None):
+    """n_steps RK3 steps of independent 1D problems; ``status_per_problem`` (int32, host or device,
+    optional) receives each problem's wt_status, and then a failed problem does not fail the call."""
     arr = (WtSegment * len(segs))(*segs)
     up, _ = _ptr(u_packed)
     tp, _ = _ptr(t_per_problem)
+    sp, _ = _ptr(status_per_problem)
     wp, _ = _ptr(ws)
-    _check(lib().weno_theta_step_batched(ctypes.byref(prob), arr, len(segs), up, total, cfl, n_steps, tp, wp,
+    _check(lib().weno_theta_step_batched(ctypes.byref(prob), arr, len(segs), up, total, cfl, n_steps, tp, sp, wp,
                                          _nbytes(ws), _stream(stream, u_packed, ws)))
 
 

@@ -33,10 +33,10 @@ int fail(int code, const char* fmt, ...) {
     if (e_ != cudaSuccess) return fail(WT_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
   } while (0)
 
-constexpr size_t kAlign = 256;
-// the step-blocked kernel reads each CTA's alpha words as one aligned 32-byte record
-static_assert(kAlign % 32 == 0, "workspace regions must start 32-byte aligned");
-inline size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+}  // namespace
+
+// Argument checks and launch defaults shared with the no-allocation entry point (wt_launch.h).
+namespace wt {
 
 int expected_m(int flux) {
   switch (flux) {
@@ -96,6 +96,43 @@ int check_grid_1d(const wt_problem* p, const wt_grid* g) {
   if (!(g->hi[0] > g->lo[0]) || !std::isfinite(g->hi[0] - g->lo[0])) return fail(WT_ERR_ARG, "need lo < hi");
   return WT_OK;
 }
+
+int default_tile(int flux, long long n) {
+  if (flux == WT_FLUX_EULER1D) {
+    // about one CTA per SM for short grids, larger tiles once the grid fills the GPU
+    if (n <= 152LL * 31) return 31;
+    if (n <= 152LL * 4 * 63) return 63;
+    return 127;
+  }
+  return n <= 152LL * 2 * 63 ? 63 : 127;
+}
+
+Stage1DArgs base_args(const wt_problem* p, long long n, double dx, long long pitch, Ctl* ctl) {
+  Stage1DArgs a;
+  memset(&a, 0, sizeof a);
+  a.n = n;
+  a.pitch = pitch;
+  a.lout_stride = n;
+  a.dx = dx;
+  a.inv_dx = 1.0 / dx;
+  a.gamma = p->gamma;
+  a.adv_speed = p->adv_speed;
+  a.eps = p->eps;
+  a.alpha_R = p->alpha_R;
+  a.bc_lo = p->bc_lo[0];
+  a.bc_hi = p->bc_hi[0];
+  a.ctl = ctl;
+  return a;
+}
+
+}  // namespace wt
+
+namespace {
+
+constexpr size_t kAlign = 256;
+// the step-blocked kernel reads each CTA's alpha words as one aligned 32-byte record
+static_assert(kAlign % 32 == 0, "workspace regions must start 32-byte aligned");
+inline size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
 // padded plane stride: n + 2G rounded up to 32 doubles (256 bytes)
 inline long long plane_pitch(long long n) { return ((n + 2 * G + 31) / 32) * 32; }
@@ -178,34 +215,6 @@ int check_ws(void* ws, size_t ws_bytes, size_t need, int* device) {
   pointer_info(ws, &dev, device);
   if (!dev) return fail(WT_ERR_WORKSPACE, "workspace is not device memory");
   return WT_OK;
-}
-
-int default_tile(int flux, long long n) {
-  if (flux == WT_FLUX_EULER1D) {
-    // about one CTA per SM for short grids, larger tiles once the grid fills the GPU
-    if (n <= 152LL * 31) return 31;
-    if (n <= 152LL * 4 * 63) return 63;
-    return 127;
-  }
-  return n <= 152LL * 2 * 63 ? 63 : 127;
-}
-
-Stage1DArgs base_args(const wt_problem* p, long long n, double dx, long long pitch, Ctl* ctl) {
-  Stage1DArgs a;
-  memset(&a, 0, sizeof a);
-  a.n = n;
-  a.pitch = pitch;
-  a.lout_stride = n;
-  a.dx = dx;
-  a.inv_dx = 1.0 / dx;
-  a.gamma = p->gamma;
-  a.adv_speed = p->adv_speed;
-  a.eps = p->eps;
-  a.alpha_R = p->alpha_R;
-  a.bc_lo = p->bc_lo[0];
-  a.bc_hi = p->bc_hi[0];
-  a.ctl = ctl;
-  return a;
 }
 
 cudaError_t launch_stage(const wt_problem* p, int stage, int tile, const Stage1DArgs& a, cudaStream_t st) {
@@ -941,8 +950,8 @@ int weno_theta_step(const wt_problem* prob, const wt_grid* grid, double* u, doub
 }
 
 int weno_theta_step_batched(const wt_problem* prob, const wt_segment* segs, int32_t nprob, double* u_packed,
-                            int64_t total, double cfl, int64_t n_steps, double* t_per_problem, void* ws,
-                            size_t ws_bytes, void* stream) {
+                            int64_t total, double cfl, int64_t n_steps, double* t_per_problem,
+                            int32_t* status_per_problem, void* ws, size_t ws_bytes, void* stream) {
   int rc;
   if ((rc = check_problem(prob)) != WT_OK) return rc;
   if (prob->flux == WT_FLUX_EULER2D) return fail(WT_ERR_UNSUPPORTED, "batched stepping supports the 1D fluxes only");
@@ -996,10 +1005,11 @@ int weno_theta_step_batched(const wt_problem* prob, const wt_segment* segs, int3
   if ((rc = check_ws(ws, ws_bytes, lay.total, &dev)) != WT_OK) return rc;
   DeviceGuard guard;
   if ((rc = guard.enter(dev)) != WT_OK) return rc;
-  bool u_dev, t_dev = false;
-  int d_u, d_t;
+  bool u_dev, t_dev = false, s_dev = false;
+  int d_u, d_t, d_s;
   pointer_info(u_packed, &u_dev, &d_u);
   if (t_per_problem) pointer_info(t_per_problem, &t_dev, &d_t);
+  if (status_per_problem) pointer_info(status_per_problem, &s_dev, &d_s);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   char* w = static_cast<char*>(ws);
   Ctl* ctl = reinterpret_cast<Ctl*>(w + lay.ctl);
@@ -1108,14 +1118,21 @@ int weno_theta_step_batched(const wt_problem* prob, const wt_segment* segs, int3
   std::vector<Ctl> back(nprob);
   WT_CUDA(cudaMemcpyAsync(back.data(), ctl, sizeof(Ctl) * nprob, cudaMemcpyDeviceToHost, st));
   WT_CUDA(cudaStreamSynchronize(st));
+  int nfail = 0, first = -1;
   for (int p = 0; p < nprob; ++p)
-    if (back[p].status != 0)
-      return fail(back[p].status, "problem %d: device reported status %d after %lld steps", p, back[p].status,
-                  back[p].steps);
+    if (back[p].status != 0 && nfail++ == 0) first = p;
+  // Without a status array one failure fails the call (and u is untouched).  With one, each
+  // problem's status goes there: the problems that succeeded are written back, the others keep
+  // their input state.
+  if (nfail > 0 && !status_per_problem)
+    return fail(back[first].status, "problem %d: device reported status %d after %lld steps (%d problems failed)",
+                first, back[first].status, back[first].steps, nfail);
+  const Ctl* skip = nfail > 0 ? ctl : nullptr;
   if (u_dev) {
-    WT_CUDA(launch_unpack1d_batched(Un, pitch, u_packed, total, dsegs, nprob, maxn, m, st));
+    WT_CUDA(launch_unpack1d_batched(Un, pitch, u_packed, total, dsegs, nprob, maxn, m, st, skip));
   } else {
-    WT_CUDA(launch_unpack1d_batched(Un, pitch, st_u, total, dsegs, nprob, maxn, m, st));
+    // st_u still holds the caller's input, so skipped problems copy back unchanged
+    WT_CUDA(launch_unpack1d_batched(Un, pitch, st_u, total, dsegs, nprob, maxn, m, st, skip));
     WT_CUDA(cudaMemcpyAsync(u_packed, st_u, sizeof(double) * m * total, cudaMemcpyDeviceToHost, st));
   }
   if (t_per_problem) {
@@ -1125,7 +1142,16 @@ int weno_theta_step_batched(const wt_problem* prob, const wt_segment* segs, int3
       for (int p = 0; p < nprob; ++p) t_per_problem[p] = back[p].t;
     }
   }
+  if (status_per_problem) {
+    if (s_dev) {
+      WT_CUDA(launch_gather_status(ctl, nprob, status_per_problem, st));
+    } else {
+      for (int p = 0; p < nprob; ++p) status_per_problem[p] = back[p].status;
+    }
+  }
   WT_CUDA(cudaStreamSynchronize(st));
+  if (nfail > 0) fail(WT_OK, "%d of %d problems failed (first: problem %d, status %d); see status_per_problem", nfail,
+                      nprob, first, back[first].status);
   return WT_OK;
 }
 

@@ -73,8 +73,12 @@ __global__ void pack1d_batched_kernel(const double* __restrict__ src, long long 
   }
 }
 
+// skip (may be null): problems whose control block carries a failure are not written, so the
+// destination keeps what it held (the caller's input state)
 __global__ void unpack1d_batched_kernel(const double* __restrict__ src, long long pitch, double* __restrict__ dst,
-                                        long long dst_stride, const BatchSeg* __restrict__ segs, int m) {
+                                        long long dst_stride, const BatchSeg* __restrict__ segs, int m,
+                                        const Ctl* __restrict__ skip) {
+  if (skip && skip[blockIdx.y].status != 0) return;
   const BatchSeg sg = segs[blockIdx.y];
   const long long total = (long long)m * sg.n;
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -90,6 +94,11 @@ __global__ void gather_t_kernel(const Ctl* __restrict__ ctl, int nprob, double* 
   if (p < nprob) t_out[p] = ctl[p].t;
 }
 
+__global__ void gather_status_kernel(const Ctl* __restrict__ ctl, int nprob, int* __restrict__ out) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < nprob) out[p] = ctl[p].status;
+}
+
 static dim3 batched_grid(long long maxn, int m, int nprob) {
   long long bx = ((long long)m * (maxn + 2 * G) + 255) / 256;
   if (bx > 64) bx = 64;
@@ -103,8 +112,15 @@ cudaError_t launch_pack1d_batched(const double* src, long long src_stride, doubl
 }
 
 cudaError_t launch_unpack1d_batched(const double* src, long long pitch, double* dst, long long dst_stride,
-                                    const BatchSeg* segs, int nprob, long long maxn, int m, cudaStream_t st) {
-  unpack1d_batched_kernel<<<batched_grid(maxn, m, nprob), 256, 0, st>>>(src, pitch, dst, dst_stride, segs, m);
+                                    const BatchSeg* segs, int nprob, long long maxn, int m, cudaStream_t st,
+                                    const Ctl* skip_failed) {
+  unpack1d_batched_kernel<<<batched_grid(maxn, m, nprob), 256, 0, st>>>(src, pitch, dst, dst_stride, segs, m,
+                                                                        skip_failed);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_status(const Ctl* ctl, int nprob, int* out, cudaStream_t st) {
+  gather_status_kernel<<<(nprob + 255) / 256, 256, 0, st>>>(ctl, nprob, out);
   return cudaGetLastError();
 }
 

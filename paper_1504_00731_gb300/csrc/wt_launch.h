@@ -70,9 +70,12 @@ cudaError_t launch_alpha1d_batched_fast(int flux, const double* u, long long pit
                                         long long maxn, double gamma, double adv, Ctl* ctl, cudaStream_t st);
 cudaError_t launch_pack1d_batched(const double* src, long long src_stride, double* dst, long long pitch,
                                   const BatchSeg* segs, int nprob, long long maxn, int m, int flip_comp, cudaStream_t st);
+// skip_failed (may be null): leave out the problems whose control block records a failure
 cudaError_t launch_unpack1d_batched(const double* src, long long pitch, double* dst, long long dst_stride,
-                                    const BatchSeg* segs, int nprob, long long maxn, int m, cudaStream_t st);
+                                    const BatchSeg* segs, int nprob, long long maxn, int m, cudaStream_t st,
+                                    const Ctl* skip_failed = nullptr);
 cudaError_t launch_gather_t(const Ctl* ctl, int nprob, double* t_out, cudaStream_t st);
+cudaError_t launch_gather_status(const Ctl* ctl, int nprob, int* out, cudaStream_t st);
 
 // Arguments of one fused 2D stage launch.  Padded planes: cell (x, y) at (y + G) * rowp + x + G.
 struct Stage2DArgs {
@@ -158,6 +161,14 @@ cudaError_t launch_selftest_wait(int which, unsigned long long* word, unsigned l
 
 // Records a message for wt_last_error() on the calling thread and returns code.
 int set_last_error(int code, const char* msg);
+
+// Argument checks of the C ABI (WT_OK, or the status with wt_last_error() set), and the
+// launch defaults every 1D RHS evaluation uses, so that entry points sharing them launch the
+// same kernel instance on the same arguments.
+int check_problem(const wt_problem* p);
+int check_grid_1d(const wt_problem* p, const wt_grid* g);  // 2D grids too, for WT_FLUX_EULER2D
+int default_tile(int flux, long long n);                  // stage-kernel tile for n cells
+Stage1DArgs base_args(const wt_problem* p, long long n, double dx, long long pitch, Ctl* ctl);
 
 cudaError_t launch_persist1d_strict(int flux, int tile, const PersistArgs& p, int grid, cudaStream_t st);
 cudaError_t launch_persist1d_fast(int flux, int tile, const PersistArgs& p, int grid, cudaStream_t st);

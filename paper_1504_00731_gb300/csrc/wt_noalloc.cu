@@ -72,28 +72,19 @@ bool is_device_pointer(const void* p, int* dev) {
 extern "C" {
 
 int weno_theta_rhs_noalloc(const wt_problem* prob, const wt_grid* grid, const double* u, double* L, void* stream) {
-  if (!prob || !grid || !u || !L) return set_error(WT_ERR_ARG, "problem, grid, u and L must not be NULL");
-  if (prob->flux != WT_FLUX_ADVECTION && prob->flux != WT_FLUX_BURGERS && prob->flux != WT_FLUX_EULER1D)
+  // the checks of weno_theta_rhs first, then the limits of this variant
+  int rc = check_problem(prob);
+  if (rc != WT_OK) return rc;
+  if ((rc = check_grid_1d(prob, grid)) != WT_OK) return rc;
+  if (!u || !L) return set_error(WT_ERR_ARG, "u and L must not be NULL");
+  if (prob->flux == WT_FLUX_EULER2D)
     return set_error(WT_ERR_UNSUPPORTED, "weno_theta_rhs_noalloc supports the 1D fluxes only");
-  const int m = prob->flux == WT_FLUX_EULER1D ? 3 : 1;
-  if (prob->m != m || grid->ndim != 1 || grid->reserved != 0 ||
-      (prob->launch != WT_LAUNCH_AUTO && prob->launch != WT_LAUNCH_STAGES))
-    return set_error(WT_ERR_ARG, "inconsistent problem or grid");
-  if (prob->mode != WT_MODE_FAST && prob->mode != WT_MODE_STRICT) return set_error(WT_ERR_ARG, "unknown mode");
-  if (!(prob->eps > 0.0) || !(prob->alpha_R >= 0.0) || (m == 3 && !(prob->gamma > 1.0)))
-    return set_error(WT_ERR_ARG, "eps, alpha_R or gamma out of range");
-  const int blo = prob->bc_lo[0], bhi = prob->bc_hi[0];
-  if (blo < 0 || blo > 2 || bhi < 0 || bhi > 2 || ((blo == WT_BC_PERIODIC) != (bhi == WT_BC_PERIODIC)))
-    return set_error(WT_ERR_ARG, "invalid boundary conditions");
-  if (m == 1 && (blo == WT_BC_REFLECTIVE || bhi == WT_BC_REFLECTIVE))
-    return set_error(WT_ERR_UNSUPPORTED, "reflective boundaries are defined for the Euler equations only");
+  const int m = prob->m;
   const long long n = grid->n[0];
-  if (n < G) return set_error(WT_ERR_ARG, "n is below the minimum of 3 cells");
   if (n > max_cells(m))
     return set_error(WT_ERR_ARG,
                      "n exceeds the built-in scratch array of WT_NOALLOC_SCRATCH_BYTES (at most 349498 cells for "
                      "Euler, 1048506 for a scalar flux); use weno_theta_rhs with a workspace");
-  if (!(grid->hi[0] > grid->lo[0])) return set_error(WT_ERR_ARG, "need lo < hi");
   int dev_u = -1, dev_L = -1;
   if (!is_device_pointer(u, &dev_u) || !is_device_pointer(L, &dev_L) || dev_u != dev_L)
     return set_error(WT_ERR_ARG, "u and L must be device memory on the same GPU");
@@ -101,39 +92,27 @@ int weno_theta_rhs_noalloc(const wt_problem* prob, const wt_grid* grid, const do
   if (cudaGetDevice(&cur) != cudaSuccess) return set_error(WT_ERR_CUDA, "cudaGetDevice failed");
   if (cur != dev_u && cudaSetDevice(dev_u) != cudaSuccess) return set_error(WT_ERR_CUDA, "cudaSetDevice failed");
   double* base = nullptr;
-  int rc = scratch_for_device(dev_u, &base);
+  rc = scratch_for_device(dev_u, &base);
   if (rc == WT_OK) {
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     Ctl* ctl = reinterpret_cast<Ctl*>(base);
     double* Un = base + kCtlDoubles;
     const long long pitch = ((n + 2 * G + 31) / 32) * 32;
     const double dx = (grid->hi[0] - grid->lo[0]) / (double)n;
-    Stage1DArgs a;
-    memset(&a, 0, sizeof a);
+    // the same arguments, tile and launches as weno_theta_rhs with a device workspace
+    Stage1DArgs a = base_args(prob, n, dx, pitch, ctl);
     a.uin = Un;
     a.Lout = L;
-    a.n = n;
-    a.pitch = pitch;
-    a.lout_stride = n;
-    a.dx = dx;
-    a.inv_dx = 1.0 / dx;
-    a.gamma = prob->gamma;
-    a.adv_speed = prob->adv_speed;
-    a.eps = prob->eps;
-    a.alpha_R = prob->alpha_R;
-    a.bc_lo = blo;
-    a.bc_hi = bhi;
-    a.ctl = ctl;
     const bool strict = prob->mode == WT_MODE_STRICT;
-    const int tile = m == 3 ? (n <= 152LL * 31 ? 31 : (n <= 152LL * 4 * 63 ? 63 : 127)) : (n <= 152LL * 2 * 63 ? 63 : 127);
+    const int blo = prob->bc_lo[0], bhi = prob->bc_hi[0];
     cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(Ctl), st);  // alpha slots and status start at zero
     if (e == cudaSuccess) e = launch_pack1d(u, n, Un, n, pitch, m, blo, bhi, 1, st);
     if (e == cudaSuccess)
       e = strict ? launch_alpha1d_strict(prob->flux, Un, n, pitch, prob->gamma, prob->adv_speed, ctl, 0, st)
                  : launch_alpha1d_fast(prob->flux, Un, n, pitch, prob->gamma, prob->adv_speed, ctl, 0, st);
     if (e == cudaSuccess)
-      e = strict ? launch_stage1d_strict(prob->flux, STAGE_RHS, tile, a, st)
-                 : launch_stage1d_fast(prob->flux, STAGE_RHS, tile, a, st);
+      e = strict ? launch_stage1d_strict(prob->flux, STAGE_RHS, default_tile(prob->flux, n), a, st)
+                 : launch_stage1d_fast(prob->flux, STAGE_RHS, default_tile(prob->flux, n), a, st);
     if (e != cudaSuccess) rc = set_error(WT_ERR_CUDA, cudaGetErrorString(e));
   }
   if (cur != dev_u) cudaSetDevice(cur);

@@ -21,6 +21,17 @@ def test_reference_arm_prints_one_json_line(oracle):
         assert k in d, k
     assert d["impl"] == "reference" and d["unit"] == "cell-updates/s" and d["higher_is_better"] is True
     assert d["value"] > 0 and d["cpu_baseline"]["value"] == d["value"] and d["e2e"]["value"] == d["value"]
-    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["cpu_baseline"]["nproc"] >= 1 and d["cpu_baseline"]["lscpu_model"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
-    assert d["config"]["workload"].startswith("euler1d_riemann_entropy_N4096")
+    assert d["config"]["workload"].startswith("euler1d_batch4096")
+
+
+def test_reference_arm_uses_the_benchmark_config():
+    """The two arms describe the same workload: the reference line's config is the one the GPU
+    line prints."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    assert bench.config_dict(1)["problems"] == 4096 and bench.config_dict(2)["problems"] == 8192
+    assert bench.RK_STEPS == 20 * bench.RK_PER_STEP  # 20 benchmark steps are the whole run

@@ -137,3 +137,20 @@ def test_full_size_step_properties(wtlib, c4_state):
     shifted = torch.roll(torch.from_numpy(U).cuda(), shifts=(3, 5), dims=(1, 2)).contiguous()
     b.weno_theta_step(prob, g, shifted, 0.45, ws, max_steps=2)
     assert torch.equal(torch.roll(u, shifts=(3, 5), dims=(1, 2)), shifted)
+
+
+def test_cropped_workload_full_length(wtlib, oracle):
+    """The 2D workload's generator (four quadrant states and eight isentropic vortices, periodic)
+    at 256 x 256, run for its full 500 RK steps at CFL 0.45 in the benchmark's fast mode: the
+    final state within 1e-10 in L1 of the oracle's (OpenMP over rows and columns), and the same
+    time reached."""
+    b, O = wtlib, oracle
+    n, steps = 256, 500
+    U, dx, dy = W.euler2d_vortices(n, n, seed=0)
+    u, t, s = _gpu_run(b, _gprob(b, 0, 0, b.WT_MODE_FAST, W.ALPHA_R_SEEDED), U, cfl=0.45, max_steps=steps)
+    ref, t_ref, s_ref = O.run(_oprob(O, 0, 0, W.ALPHA_R_SEEDED), U, dx, dy, cfl=0.45, n_steps=steps)
+    assert s == s_ref == steps
+    assert abs(t - t_ref) <= 1e-12 * t_ref
+    assert np.isfinite(u).all()
+    l1 = dx * dy * np.abs(u - ref).reshape(4, -1).sum(axis=1)
+    assert np.all(l1 <= SHOCK_L1_TOL), l1
