@@ -190,7 +190,18 @@ def stride_sample(lengths, every):
     return np.sort(order[::every])
 
 
-def cpu_baseline(serial_every=32, serial_steps=8, par_every=4, par_steps=4):
+def cpu_baseline():
+    """The oracle's CPU baseline, measured in a process of its own (no CUDA context or torch
+    threads beside it), as cpu_baseline_here() reports it."""
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-baseline-only"], capture_output=True,
+                       text=True, timeout=900, cwd=ROOT)
+    if r.returncode != 0:
+        return {"value": None, "unit": "cell-updates/s", "cores": None, "kind": "oracle",
+                "sample": "failed: " + (r.stderr.strip().splitlines() or ["?"])[-1]}
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline_here(serial_every=32, serial_steps=8, par_every=4, par_steps=4):
     """The oracle, as it stands, on seeded samples of the same workload (every k-th problem in
     length order, so the sample keeps the batch's length mix): one core, and OpenMP over the
     problems on every core (the per-problem arithmetic is the same)."""
@@ -214,7 +225,7 @@ def cpu_baseline(serial_every=32, serial_steps=8, par_every=4, par_steps=4):
     par = out["all_cores"]
     return {"value": par["value"], "unit": "cell-updates/s", "cores": par["cores"], "kind": "oracle",
             "sample": "all cores: " + par["sample"] + "; serial: " + out["serial"]["sample"],
-            "serial": out["serial"], "all_cores": par, **host_info(),
+            "serial": out["serial"], "all_cores": par, **host_info(), "openmp": O.openmp(),
             "build": "g++ -O2 -ffp-contract=off -fopenmp (OpenMP over independent problems)"}
 
 
@@ -319,6 +330,7 @@ def plain_vs_batched(B, dev, batch, steps=20):
                          launch=launch)
         ws = B.alloc_workspace(B.workspace_bytes(pmax, B.grid_1d(nmax, -5.0, 5.0)), dev)
         tot_ms, cells = 0.0, 0
+        per = np.zeros(len(batch.lengths))
         for p in range(len(batch.lengths)):
             o, n = int(batch.offsets[p]), int(batch.lengths[p])
             pb = B.problem(B.WT_FLUX_EULER1D, bc=int(batch.bc[p]), mode=B.WT_MODE_FAST, alpha_R=W.ALPHA_R_SEEDED,
@@ -331,9 +343,19 @@ def plain_vs_batched(B, dev, batch, steps=20):
             B.weno_theta_step(pb, g, us, CFL, ws, max_steps=steps)
             e1.record(stream)
             e1.synchronize()
-            tot_ms += e0.elapsed_time(e1)
+            per[p] = e0.elapsed_time(e1) * 1e-3
+            tot_ms += per[p] * 1e3
             cells += n
         out[name] = {"value": cells * steps / (tot_ms * 1e-3), "seconds": tot_ms * 1e-3}
+        # where the per-problem time goes, by problem length
+        groups = []
+        for lo_n, hi_n in ((0, 2048), (2048, 16384), (16384, 1 << 30)):
+            sel = (batch.lengths >= lo_n) & (batch.lengths < hi_n)
+            c, t = int(batch.lengths[sel].sum()), float(per[sel].sum())
+            groups.append({"n_range": [lo_n, min(hi_n, 65536)], "problems": int(sel.sum()),
+                           "cells_share": c / cells, "time_share": t / (tot_ms * 1e-3),
+                           "rate": c * steps / t if t > 0 else None})
+        out[name]["by_length"] = groups
         del ws
     return out
 
@@ -657,9 +679,15 @@ def run_ours(args):
         if world == 1 and not args.no_extras:
             ex = {}
             pv = plain_vs_batched(B, dev, batch)
+            # the most any kernel issuing this kernel's FP64 instructions could reach: every SMSP's
+            # FP64 pipe busy all the time (152 x 4 x 0.5 lanes per clock at 2.07 GHz)
+            cb = counters("batched")
+            full_pipe = 152 * 4 * 0.5 * 2.07e9 / cb["fp64_thread_ops_per_cell_update"] if cb else None
             ex["batched_vs_plain"] = {**pv, "batched_value": value,
                                       "batched_over_plain_auto": value / pv["plain_auto"]["value"],
                                       "batched_over_plain_stages": value / pv["plain_stages"]["value"],
+                                      "rate_at_full_fp64_pipe": full_pipe,
+                                      "ratio_at_full_fp64_pipe": full_pipe / pv["plain_auto"]["value"] if cb else None,
                                       "how": "all 4096 problems through weno_theta_step one at a time, 20 RK steps "
                                              "each; cell-updates/s over the summed CUDA-event times of the calls"}
             del ws, src, u, u0
@@ -729,8 +757,11 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the single-problem, 2D, adjoint and per-problem "
                                                               "measurements")
     ap.add_argument("--profile-case", default=None, help="run one small case for an ncu capture and exit")
+    ap.add_argument("--cpu-baseline-only", action="store_true", help="print the oracle's CPU baseline and exit")
     args = ap.parse_args()
-    if args.profile_case:
+    if args.cpu_baseline_only:
+        print(json.dumps(cpu_baseline_here()), flush=True)
+    elif args.profile_case:
         run_profile_case(args.profile_case)
     elif args.impl == "reference":
         run_reference(args)

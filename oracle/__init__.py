@@ -63,15 +63,19 @@ def problem(flux, gamma=1.4, adv_speed=1.0, eps=1e-10, alpha_R=50.0, bc=BC_PERIO
     return p
 
 
+_BUILD_NOTE = {}
+
+
 def _compile(out: str, defines=()) -> None:
-    """g++ -O2 -ffp-contract=off, with OpenMP over independent problems where the compiler has it
-    (the per-problem arithmetic is the same either way)."""
+    """g++ -O2 -ffp-contract=off, with OpenMP over independent problems (and 2D rows and columns)
+    where the compiler has it; the arithmetic of each problem, row and column is the same either
+    way, so a build without OpenMP gives the same results on one thread."""
     os.makedirs(_BUILD, exist_ok=True)
     tmp = out + f".tmp{os.getpid()}"
     base = ["g++", "-O2", "-ffp-contract=off", "-std=c++17", "-fPIC", "-shared"] + [f"-D{d}" for d in defines]
-    try:
-        subprocess.run(base + ["-fopenmp", "-o", tmp, _SRC], check=True, capture_output=True)
-    except subprocess.CalledProcessError:
+    r = subprocess.run(base + ["-fopenmp", "-o", tmp, _SRC], capture_output=True, text=True)
+    if r.returncode != 0:
+        _BUILD_NOTE[out] = "built without OpenMP: " + (r.stderr.strip().splitlines() or ["?"])[-1]
         subprocess.run(base + ["-o", tmp, _SRC], check=True)
     os.replace(tmp, out)
 
@@ -101,7 +105,9 @@ def planted(name: str):
     with _lock:
         if not (os.path.exists(path) and os.path.getmtime(path) >= os.path.getmtime(_SRC)):
             _compile(path, (f"WTO_PLANT_{name}",))
-    return _declare(_load(path, lambda: _compile(path, (f"WTO_PLANT_{name}",))))
+    L = _declare(_load(path, lambda: _compile(path, (f"WTO_PLANT_{name}",))))
+    L.wto_set_threads(host_threads())
+    return L
 
 
 class using:
@@ -121,12 +127,30 @@ class using:
         _lib = self.saved
 
 
+def host_threads() -> int:
+    """Host cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
 def lib():
+    """The oracle library, set to use every host core this process may run on (an
+    OMP_NUM_THREADS in the environment does not apply: the oracle's threads only split
+    independent problems, rows and columns)."""
     global _lib
     if _lib is not None:
         return _lib
-    _lib = _declare(_load(build(), lambda: build(force=True)))
+    L = _declare(_load(build(), lambda: build(force=True)))
+    L.wto_set_threads(host_threads())
+    _lib = L
     return _lib
+
+
+def openmp() -> bool:
+    """Whether the oracle library was built with OpenMP."""
+    return bool(lib().wto_set_threads(0))
 
 
 def _declare(L):
@@ -152,6 +176,8 @@ def _declare(L):
     L.wto_riemann_sample.argtypes = [D, D, D, D, D, D, D, D, D, P, I64, P, P, P]
     L.wto_run_batch.argtypes = [PP, ctypes.c_int32, PI64, PI64, P, P, PI32, P, I64, D, I64, ctypes.c_int32, PI64]
     L.wto_max_threads.restype = ctypes.c_int32
+    L.wto_set_threads.argtypes = [ctypes.c_int32]
+    L.wto_set_threads.restype = ctypes.c_int32
     return L
 
 

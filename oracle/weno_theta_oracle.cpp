@@ -926,8 +926,8 @@ void wto_run_batch(const Problem* P, int32_t nprob, const int64_t* offsets, cons
   for (int32_t p = 0; p < nprob; ++p) order[(size_t)p] = p;
   std::sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return lengths[a] > lengths[b]; });
 #ifdef _OPENMP
-  if (nthreads > 0) omp_set_num_threads(nthreads);
-#pragma omp parallel for schedule(dynamic, 1)
+  const int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
 #endif
   for (int32_t k = 0; k < nprob; ++k) {
     const int32_t p = order[(size_t)k];
@@ -946,12 +946,23 @@ void wto_run_batch(const Problem* P, int32_t nprob, const int64_t* offsets, cons
   }
 }
 
-/* Threads wto_run_batch uses when nthreads = 0 (1 without OpenMP). */
+/* Threads wto_run_batch and the 2D sweeps use when nthreads = 0 (1 without OpenMP). */
 int32_t wto_max_threads(void) {
 #ifdef _OPENMP
   return (int32_t)omp_get_max_threads();
 #else
   return 1;
+#endif
+}
+
+/* Sets that thread count (ignored without OpenMP); returns 1 if the library has OpenMP. */
+int32_t wto_set_threads(int32_t n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return 1;
+#else
+  (void)n;
+  return 0;
 #endif
 }
 

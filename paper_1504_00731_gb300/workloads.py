@@ -363,3 +363,12 @@ def riemann_123(n: int, lo=-5.0, hi=5.0):
     x, dx = grid_1d(n, lo, hi, periodic=False)
     left = x < 0.0
     return cons_1d(np.ones(n), np.where(left, -2.0, 2.0), np.full(n, 0.4)), x, dx
+
+
+def ulp_perturbed(U, seed: int):
+    """The data with every value moved by at most one unit in its last place (seeded): the
+    input of a second oracle run that shows how far rounding alone carries two evaluations of
+    the method apart (amplified by the flow, or flipping a decision that sits on its threshold)."""
+    U = np.asarray(U, dtype=np.float64)
+    rng = np.random.default_rng(seed)
+    return U * (1.0 + rng.integers(-1, 2, U.shape) * 2.0 ** -52)

@@ -139,18 +139,34 @@ def test_full_size_step_properties(wtlib, c4_state):
     assert torch.equal(torch.roll(u, shifts=(3, 5), dims=(1, 2)), shifted)
 
 
+def _ulp_spread(O, P, U, dx, dy, steps, cfl, ref):
+    """L1 distance, per component, between the oracle's run and its run from the same data with
+    every value moved by at most one unit in the last place: how far rounding alone carries two
+    evaluations of the method apart on this flow after `steps` steps."""
+    other, _, _ = O.run(P, W.ulp_perturbed(U, 1), dx, dy, cfl=cfl, n_steps=steps)
+    return dx * dy * np.abs(other - ref).reshape(4, -1).sum(axis=1)
+
+
 def test_cropped_workload_full_length(wtlib, oracle):
     """The 2D workload's generator (four quadrant states and eight isentropic vortices, periodic)
-    at 256 x 256, run for its full 500 RK steps at CFL 0.45 in the benchmark's fast mode: the
-    final state within 1e-10 in L1 of the oracle's (OpenMP over rows and columns), and the same
-    time reached."""
+    at 256 x 256, run for its full 500 RK steps at CFL 0.45.  Strict mode equals the oracle bit for
+    bit at the final time.  Fast mode (the benchmark's) is within 1e-10 in L1 after 200 steps; by
+    500 steps the flow has amplified rounding differences of every kind (two oracle runs whose data
+    differ by one ulp drift apart the same way, to about 6e-9), so there it is held to ten times
+    that spread."""
     b, O = wtlib, oracle
-    n, steps = 256, 500
+    n, steps, cfl = 256, 500, 0.45
     U, dx, dy = W.euler2d_vortices(n, n, seed=0)
-    u, t, s = _gpu_run(b, _gprob(b, 0, 0, b.WT_MODE_FAST, W.ALPHA_R_SEEDED), U, cfl=0.45, max_steps=steps)
-    ref, t_ref, s_ref = O.run(_oprob(O, 0, 0, W.ALPHA_R_SEEDED), U, dx, dy, cfl=0.45, n_steps=steps)
-    assert s == s_ref == steps
-    assert abs(t - t_ref) <= 1e-12 * t_ref
-    assert np.isfinite(u).all()
-    l1 = dx * dy * np.abs(u - ref).reshape(4, -1).sum(axis=1)
-    assert np.all(l1 <= SHOCK_L1_TOL), l1
+    P = _oprob(O, 0, 0, W.ALPHA_R_SEEDED)
+    ref, t_ref, s_ref = O.run(P, U, dx, dy, cfl=cfl, n_steps=steps)
+    us, ts, ss = _gpu_run(b, _gprob(b, 0, 0, b.WT_MODE_STRICT, W.ALPHA_R_SEEDED), U, cfl=cfl, max_steps=steps)
+    assert ss == s_ref == steps and ts == t_ref
+    assert np.array_equal(us, ref)
+    uf, tf, sf = _gpu_run(b, _gprob(b, 0, 0, b.WT_MODE_FAST, W.ALPHA_R_SEEDED), U, cfl=cfl, max_steps=steps)
+    assert sf == steps and abs(tf - t_ref) <= 1e-12 * t_ref and np.isfinite(uf).all()
+    spread = _ulp_spread(O, P, U, dx, dy, steps, cfl, ref)
+    l1 = dx * dy * np.abs(uf - ref).reshape(4, -1).sum(axis=1)
+    assert np.all(l1 <= np.maximum(10.0 * spread, SHOCK_L1_TOL)), (l1, spread)
+    ref200, _, _ = O.run(P, U, dx, dy, cfl=cfl, n_steps=200)
+    u200, _, _ = _gpu_run(b, _gprob(b, 0, 0, b.WT_MODE_FAST, W.ALPHA_R_SEEDED), U, cfl=cfl, max_steps=200)
+    assert np.all(dx * dy * np.abs(u200 - ref200).reshape(4, -1).sum(axis=1) <= SHOCK_L1_TOL)
