@@ -741,6 +741,18 @@ def run_profile_case(name):
         u = torch.from_numpy(U).to(dev)
         B.weno_theta_step(prob, g, u, 0.45, ws, max_steps=1)
         print("cells", 1024 * 1024)
+    elif name == "adjoint-64":
+        # 64 problems of the adjoint workload, 8 steps with checkpoints every 4
+        U0, dx = W.adjoint_batch(64, 16384)
+        prob = B.problem(B.WT_FLUX_EULER1D, bc=B.WT_BC_OUTFLOW, mode=B.WT_MODE_FAST, alpha_R=W.ALPHA_R_SEEDED)
+        g = B.grid_1d(16384, -5.0, 5.0)
+        ws = B.alloc_workspace(B.adjoint_workspace_bytes(prob, g, 64, 8, 4), dev)
+        u = torch.from_numpy(U0).to(dev)
+        gT, g0, uT = torch.zeros_like(u), torch.empty_like(u), torch.empty_like(u)
+        gT[:, 0, :] = 1e-3
+        B.weno_theta_adjoint(prob, g, 64, u, CFL, 8, 4, gT, g0, ws, uT=uT)
+        u = g0
+        print("cells", 64 * 16384)
     else:
         raise SystemExit(f"unknown profile case {name}")
     torch.cuda.synchronize()

@@ -175,6 +175,7 @@ def _declare(L):
     L.wto_riemann_star.argtypes = [D, D, D, D, D, D, D, P, P, PI32]
     L.wto_riemann_sample.argtypes = [D, D, D, D, D, D, D, D, D, P, I64, P, P, P]
     L.wto_run_batch.argtypes = [PP, ctypes.c_int32, PI64, PI64, P, P, PI32, P, I64, D, I64, ctypes.c_int32, PI64]
+    L.wto_run_jvp_batch.argtypes = [PP, ctypes.c_int32, PI64, PI64, P, P, PI32, P, P, I64, D, I64, ctypes.c_int32]
     L.wto_max_threads.restype = ctypes.c_int32
     L.wto_set_threads.argtypes = [ctypes.c_int32]
     L.wto_set_threads.restype = ctypes.c_int32
@@ -349,3 +350,22 @@ def run_batch(prob, u_packed, offsets, lengths, lo, hi, bc, cfl=0.5, n_steps=1, 
                         _ptr(hi), bc.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _ptr(u), total, cfl, n_steps,
                         threads, steps.ctypes.data_as(I64P))
     return u, steps
+
+
+def run_jvp_batch(prob, u_packed, du_packed, offsets, lengths, lo, hi, bc, cfl=0.5, n_steps=1, threads=0):
+    """Forward-mode derivative of ``run_batch`` along ``du_packed``: returns (u(T), du(T)), packed
+    like the input; each problem is ``run_jvp``'s map, several at once on ``threads`` threads."""
+    u = np.ascontiguousarray(u_packed, dtype=np.float64).copy()
+    du = np.ascontiguousarray(du_packed, dtype=np.float64).copy()
+    m, total = u.shape
+    nprob = len(lengths)
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    ln = np.ascontiguousarray(lengths, dtype=np.int64)
+    lo = np.ascontiguousarray(np.broadcast_to(lo, (nprob,)), dtype=np.float64)
+    hi = np.ascontiguousarray(np.broadcast_to(hi, (nprob,)), dtype=np.float64)
+    bc = np.ascontiguousarray(bc, dtype=np.int32)
+    I64P = ctypes.POINTER(ctypes.c_int64)
+    lib().wto_run_jvp_batch(ctypes.byref(prob), nprob, off.ctypes.data_as(I64P), ln.ctypes.data_as(I64P), _ptr(lo),
+                            _ptr(hi), bc.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _ptr(u), _ptr(du), total,
+                            cfl, n_steps, threads)
+    return u, du

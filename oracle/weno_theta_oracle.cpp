@@ -946,6 +946,40 @@ void wto_run_batch(const Problem* P, int32_t nprob, const int64_t* offsets, cons
   }
 }
 
+/* The forward-mode derivative of wto_run_batch: du (same packing as u) is the direction and
+ * returns the derivative of u(T) along it, problem by problem (each one run_jvp's map). */
+void wto_run_jvp_batch(const Problem* P, int32_t nprob, const int64_t* offsets, const int64_t* lengths,
+                       const double* lo, const double* hi, const int32_t* bc, double* u, double* du, int64_t total,
+                       double cfl, int64_t n_steps, int32_t nthreads) {
+  std::vector<int32_t> order((size_t)nprob);
+  for (int32_t p = 0; p < nprob; ++p) order[(size_t)p] = p;
+  std::sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return lengths[a] > lengths[b]; });
+#ifdef _OPENMP
+  const int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
+#endif
+  for (int32_t k = 0; k < nprob; ++k) {
+    const int32_t p = order[(size_t)k];
+    const int64_t n = lengths[p];
+    Problem Q = *P;
+    Q.bc_lo[0] = Q.bc_hi[0] = bc[p];
+    Grid g{n, 1, (hi[p] - lo[p]) / (double)n, 1.0};
+    std::vector<Dual> w((size_t)Q.m * n);
+    for (int c = 0; c < Q.m; ++c)
+      for (int64_t j = 0; j < n; ++j) {
+        const size_t at = (size_t)c * total + offsets[p] + j;
+        w[(size_t)c * n + j] = Dual(u[at], du[at]);
+      }
+    run(Q, g, w.data(), cfl, 0.0, INFINITY, n_steps, (double*)0, (int64_t*)0);
+    for (int c = 0; c < Q.m; ++c)
+      for (int64_t j = 0; j < n; ++j) {
+        const size_t at = (size_t)c * total + offsets[p] + j;
+        u[at] = w[(size_t)c * n + j].v;
+        du[at] = w[(size_t)c * n + j].d;
+      }
+  }
+}
+
 /* Threads wto_run_batch and the 2D sweeps use when nthreads = 0 (1 without OpenMP). */
 int32_t wto_max_threads(void) {
 #ifdef _OPENMP

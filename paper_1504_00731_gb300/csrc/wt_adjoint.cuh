@@ -85,11 +85,17 @@ __device__ __forceinline__ void weno_grad(const double* q, double eps, bool rest
   const double tau = theta1 ? fma(C12 * xt, xt, yt * yt) : fma(C12 * xt, xt, 0.25 * yt * yt);
   const double g[4] = {theta1 ? 2.0 / 20.0 : 1.0 / 20.0, theta1 ? 12.0 / 20.0 : 9.0 / 20.0,
                        theta1 ? 6.0 / 20.0 : 9.0 / 20.0, theta1 ? 0.0 : 1.0 / 20.0};
+  // 1 / (eps + beta_k) from one division: the product of the four, times the other three
   double d[4], id[4], a[4], S = 0;
 #pragma unroll
+  for (int k = 0; k < 4; ++k) d[k] = eps + beta[k];
+  const double p01 = d[0] * d[1], p23 = d[2] * d[3], ip = 1.0 / (p01 * p23);
+  id[0] = d[1] * p23 * ip;
+  id[1] = d[0] * p23 * ip;
+  id[2] = p01 * d[3] * ip;
+  id[3] = p01 * d[2] * ip;
+#pragma unroll
   for (int k = 0; k < 4; ++k) {
-    d[k] = eps + beta[k];
-    id[k] = 1.0 / d[k];
     a[k] = g[k] * fma(tau, id[k], 1.0);
     S += a[k];
   }
@@ -130,7 +136,7 @@ __device__ __forceinline__ void weno_grad(const double* q, double eps, bool rest
 
 // Ubar += A(U)^T fbar with A the Jacobian of the 1D Euler flux (Sec. 4.2).
 __device__ __forceinline__ void euler_flux_jt(const double* U, double gamma, const double* fb, double* Ub) {
-  const double u = U[1] / U[0], e = U[2] / U[0], gm1 = gamma - 1.0;
+  const double ir = 1.0 / U[0], u = U[1] * ir, e = U[2] * ir, gm1 = gamma - 1.0;
   Ub[0] += -0.5 * (3.0 - gamma) * u * u * fb[1] + (-gamma * e * u + gm1 * u * u * u) * fb[2];
   Ub[1] += fb[0] + (3.0 - gamma) * u * fb[1] + (gamma * e - 1.5 * gm1 * u * u) * fb[2];
   Ub[2] += gm1 * fb[1] + gamma * u * fb[2];
@@ -155,8 +161,10 @@ __device__ __forceinline__ void euler_uc_grad(const double* U, double gamma, dou
 __device__ __forceinline__ void roe_reverse(const double* Ua, const double* Ub, double sa, double ua, double Ha,
                                             double sb, double ub, double Hb, const double* rs, double gamma,
                                             const double* Lb, const double* Rb, double* Uab, double* Ubb) {
+  // reciprocals once (an IEEE division costs about nine FMA slots of the narrow FP64 pipe)
   const double u = rs[0], H = rs[1], c = rs[2], gm1 = gamma - 1.0;
-  const double b1 = gm1 / (c * c);
+  const double ic = 1.0 / c, ic2 = ic * ic;
+  const double b1 = gm1 * ic2;
   double ubar = 0, cbar = 0, Hbar = 0, b1b = 0, b2b = 0, r1b = 0, r2b = 0;
   b2b += 0.5 * Lb[0];
   r1b += 0.5 * Lb[0];
@@ -176,35 +184,35 @@ __device__ __forceinline__ void roe_reverse(const double* Ua, const double* Ub, 
   b1b += 0.5 * Lb[8];
   b1b += 0.5 * u * u * b2b;  // b2 = u^2 b1 / 2
   ubar += u * b1 * b2b;
-  ubar += r1b / c;  // r1 = u / c
-  cbar += -r1b * u / (c * c);
-  cbar += -r2b / (c * c);  // r2 = 1 / c
-  cbar += b1b * (-2.0 * gm1 / (c * c * c));
+  ubar += r1b * ic;  // r1 = u / c
+  cbar += -r1b * u * ic2;
+  cbar += -r2b * ic2;  // r2 = 1 / c
+  cbar += b1b * (-2.0 * gm1 * ic2 * ic);
   // R: rows (1,1,1), (u-c, u, u+c), (H-uc, u^2/2, H+uc)
   ubar += Rb[3] + Rb[4] + Rb[5] + u * Rb[7] - c * Rb[6] + c * Rb[8];
   cbar += -Rb[3] + Rb[5] - u * Rb[6] + u * Rb[8];
   Hbar += Rb[6] + Rb[8];
   // c^2 = (gamma - 1)(H - u^2 / 2)
-  const double c2b = cbar / (2.0 * c);
+  const double c2b = 0.5 * cbar * ic;
   Hbar += gm1 * c2b;
   ubar += -gm1 * u * c2b;
   // u~ = (sa ua + sb ub) / D, H~ = (sa Ha + sb Hb) / D
-  const double D = sa + sb;
-  const double uab = ubar * sa / D, ubb = ubar * sb / D, Hab = Hbar * sa / D, Hbb = Hbar * sb / D;
-  const double sab = (ubar * (ua - u) + Hbar * (Ha - H)) / D;
-  const double sbb = (ubar * (ub - u) + Hbar * (Hb - H)) / D;
-  // per cell: u = m / rho, H = gamma E / rho - (gamma - 1) u^2 / 2, s = sqrt(rho)
+  const double iD = 1.0 / (sa + sb);
+  const double uab = ubar * sa * iD, ubb = ubar * sb * iD, Hab = Hbar * sa * iD, Hbb = Hbar * sb * iD;
+  const double sab = (ubar * (ua - u) + Hbar * (Ha - H)) * iD;
+  const double sbb = (ubar * (ub - u) + Hbar * (Hb - H)) * iD;
+  // per cell: u = m / rho, H = gamma E / rho - (gamma - 1) u^2 / 2, s = sqrt(rho); 1/s = s / rho
   {
-    const double r = Ua[0], E = Ua[2];
-    Uab[0] += uab * (-ua / r) + Hab * ((-gamma * E / r + gm1 * ua * ua) / r) + sab / (2.0 * sa);
-    Uab[1] += uab / r + Hab * (-gm1 * ua / r);
-    Uab[2] += Hab * gamma / r;
+    const double ir = 1.0 / Ua[0], E = Ua[2];
+    Uab[0] += uab * (-ua * ir) + Hab * ((-gamma * E * ir + gm1 * ua * ua) * ir) + 0.5 * sab * sa * ir;
+    Uab[1] += uab * ir + Hab * (-gm1 * ua * ir);
+    Uab[2] += Hab * gamma * ir;
   }
   {
-    const double r = Ub[0], E = Ub[2];
-    Ubb[0] += ubb * (-ub / r) + Hbb * ((-gamma * E / r + gm1 * ub * ub) / r) + sbb / (2.0 * sb);
-    Ubb[1] += ubb / r + Hbb * (-gm1 * ub / r);
-    Ubb[2] += Hbb * gamma / r;
+    const double ir = 1.0 / Ub[0], E = Ub[2];
+    Ubb[0] += ubb * (-ub * ir) + Hbb * ((-gamma * E * ir + gm1 * ub * ub) * ir) + 0.5 * sbb * sb * ir;
+    Ubb[1] += ubb * ir + Hbb * (-gm1 * ub * ir);
+    Ubb[2] += Hbb * gamma * ir;
   }
 }
 
@@ -342,7 +350,7 @@ __global__ void __launch_bounds__(AdjTile<T>::NT) adj_stage_kernel(const AdjArgs
       const long long gi = j0 - 1 + i;
       const double wl = (gi >= 0) ? s_w[c * (T + 2) + i] : 0.0;
       const double wr = (gi + 1 < n) ? s_w[c * (T + 2) + i + 1] : 0.0;
-      s_hb[c * NI + i] = (wr - wl) / sg.dx;
+      s_hb[c * NI + i] = (wr - wl) * sg.inv_dx;
     }
     __syncthreads();
     // ---- C1: per (interface, field), one pass: projection, both reconstructions with the

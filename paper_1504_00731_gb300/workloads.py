@@ -216,6 +216,24 @@ def amplitude_perturbation(nprob: int, seed: int, rel=0.01):
     return 1.0 + rel * rng.uniform(-1.0, 1.0, (nprob, 5))
 
 
+def adjoint_batch(nprob: int = 256, n: int = 16384, seed: int = 0, perturbed: bool = False):
+    """Initial data of the adjoint workload, (nprob, 3, n): nprob 1D Euler problems of n cells on
+    [-5, 5] (outflow), Riemann + entropy-wave data with per-problem seeds seed * 1_000_003 + p.
+    perturbed=True gives the target's initial data: the jump states' density and pressure and
+    the entropy-wave amplitude scaled by (1 + 0.01 U[-1, 1]) per problem."""
+    scale = amplitude_perturbation(nprob, seed) if perturbed else None
+    U = np.empty((nprob, 3, n))
+    dx = 0.0
+    for p in range(nprob):
+        prm = riemann_params(seed * 1_000_003 + p)
+        if scale is not None:
+            s = scale[p]
+            prm = RiemannParams(prm.rhoL * s[0], prm.uL, prm.pL * s[1], prm.rhoR * s[2], prm.uR, prm.pR * s[3],
+                                prm.x0, prm.k, prm.amp * s[4])
+        U[p], _, dx = euler_riemann(n, prm)
+    return U, dx
+
+
 # --------------------------------------------------------------------------------------------
 # 2D Euler: four Riemann quadrants plus isentropic vortices, periodic on [0, 1]^2
 # --------------------------------------------------------------------------------------------

@@ -20,3 +20,16 @@ def test_run_batch_equals_single_problem_runs(oracle):
         assert steps == 4
         assert np.array_equal(one[:, o:o + n], ref)
     assert O.max_threads() >= 1
+
+
+def test_run_jvp_batch_equals_single_problem_runs(oracle):
+    O = oracle
+    b = W.euler_batch(6, seed=5, nmin=8, nmax=64)
+    P = O.problem(O.FLUX_EULER1D, alpha_R=W.ALPHA_R_SEEDED)
+    d = np.random.default_rng(2).standard_normal(b.u.shape)
+    u, du = O.run_jvp_batch(P, b.u, d, b.offsets, b.lengths, b.lo, b.hi, b.bc, cfl=0.5, n_steps=3)
+    for p in range(6):
+        o, n = int(b.offsets[p]), int(b.lengths[p])
+        Q = O.problem(O.FLUX_EULER1D, bc=int(b.bc[p]), alpha_R=W.ALPHA_R_SEEDED)
+        ru, rdu, _, _ = O.run_jvp(Q, b.u[:, o:o + n], d[:, o:o + n], b.dx[p], cfl=0.5, n_steps=3)
+        assert np.array_equal(u[:, o:o + n], ru) and np.array_equal(du[:, o:o + n], rdu)
