@@ -169,6 +169,12 @@ int weno_theta_step(const wt_problem* prob, const wt_grid* grid, double* u, doub
  *                      u_packed keeps the input state, every other problem is written back
  *                      as without it (bit for bit), and the call returns WT_OK;
  *                      wt_last_error() then names how many failed.
+ * The tile of cells each CTA takes and the (interface, field) items each thread carries are
+ * chosen by timing the candidates on the first call for a given batch (keyed by flux, mode,
+ * device and the segments' lengths and boundaries) and reused afterwards; the results do not
+ * depend on the choice.  The environment variable WT_BATCHED_TILE, if set, fixes the choice to
+ * one tile code (cells per tile + 1000 x (items per thread - 1); Euler: 31, 63, 127, 1063,
+ * 1127, 2127, 3127, 5127; scalar fluxes: 63, 127), for tests and for callers that tuned offline.
  * Synchronises `stream` before returning.
  */
 int weno_theta_step_batched(const wt_problem* prob, const wt_segment* segs, int32_t nprob, double* u_packed,

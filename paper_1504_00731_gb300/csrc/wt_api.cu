@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <algorithm>
 #include <mutex>
@@ -310,12 +311,20 @@ Ctl make_ctl(double cfl, double dt_fixed, double t_final) {
 
 // --- batched stepping -------------------------------------------------------------------
 
+// Candidates of the batched autotuner, as tile codes: cells per tile + 1000 x (items per thread
+// - 1).  Euler: tiles of 31, 63 and 127 cells with one (interface, field) item per thread, 63
+// and 127 cells with two, 127 cells with three, four and six (fewer threads, more work each).
 int tile_candidates(int flux, int* out) {
   if (flux == WT_FLUX_EULER1D) {
     out[0] = 31;
     out[1] = 63;
     out[2] = 127;
-    return 3;
+    out[3] = 1063;
+    out[4] = 1127;
+    out[5] = 2127;
+    out[6] = 3127;
+    out[7] = 5127;
+    return 8;
   }
   out[0] = 63;
   out[1] = 127;
@@ -358,7 +367,8 @@ BatchLayout layout_batched(int m, int nprob, long long pitch, long long max_tile
 long long batched_pitch_bound(long long cells, int nprob) { return ((cells + 8LL * nprob + 31) / 32) * 32; }
 long long batched_tiles_bound(long long cells, int nprob) { return cells / 31 + nprob; }
 
-std::vector<int2> make_tiles(const std::vector<BatchSeg>& segs, int T) {
+std::vector<int2> make_tiles(const std::vector<BatchSeg>& segs, int code) {
+  const int T = code % 1000;  // cells per tile of the tile code
   std::vector<int2> t;
   // largest problems first, so the tail of the persistent loop is made of short work
   std::vector<int> order(segs.size());
@@ -380,8 +390,26 @@ std::vector<BatchGraph> g_bgraphs;
 struct TuneEntry {
   int flux, mode, nprob, device;
   long long total, pitch;
+  unsigned long long mix;  // hash of the segments' lengths and boundaries
   int tile;
 };
+
+// FNV-1a over the segments' lengths and boundary conditions: batches of the same size but a
+// different mix of lengths get their own autotuning
+unsigned long long segment_mix(const std::vector<BatchSeg>& segs) {
+  unsigned long long h = 1469598103934665603ull;
+  auto mixin = [&](unsigned long long v) {
+    for (int b = 0; b < 8; ++b) {
+      h ^= (v >> (8 * b)) & 0xffull;
+      h *= 1099511628211ull;
+    }
+  };
+  for (const BatchSeg& s : segs) {
+    mixin((unsigned long long)s.n);
+    mixin((unsigned long long)(s.bc_lo * 4 + s.bc_hi));
+  }
+  return h;
+}
 std::vector<TuneEntry> g_tuned;
 
 int batched_grid_size(const wt_problem* p, int tile, long long ntiles, int device) {
@@ -996,7 +1024,7 @@ int weno_theta_step_batched(const wt_problem* prob, const wt_segment* segs, int3
     cells += sg.n;
   }
   const long long pitch = ((poff + 31) / 32) * 32;
-  int cand[3];
+  int cand[8];
   const int ncand = tile_candidates(prob->flux, cand);
   long long max_tiles = 0;
   for (int p = 0; p < nprob; ++p) max_tiles += (hs[p].n + cand[0] - 1) / cand[0];
@@ -1056,11 +1084,19 @@ int weno_theta_step_batched(const wt_problem* prob, const wt_segment* segs, int3
 
   // ---- tile size: autotuned once per batch shape (timed RK stage 1 per candidate)
   int tile = -1;
-  {
+  const unsigned long long mix = segment_mix(hs);
+  // WT_BATCHED_TILE fixes the candidate (tests; callers that tuned offline)
+  if (const char* forced = getenv("WT_BATCHED_TILE")) {
+    const int code = atoi(forced);
+    for (int ci = 0; ci < ncand; ++ci)
+      if (cand[ci] == code) tile = code;
+    if (tile < 0) return fail(WT_ERR_ARG, "WT_BATCHED_TILE=%s is not a candidate for this flux", forced);
+  }
+  if (tile < 0) {
     std::lock_guard<std::mutex> lk(g_graph_mu);
     for (auto& e : g_tuned)
       if (e.flux == prob->flux && e.mode == prob->mode && e.nprob == nprob && e.device == dev && e.total == total &&
-          e.pitch == pitch)
+          e.pitch == pitch && e.mix == mix)
         tile = e.tile;
   }
   if (tile < 0 && n_steps > 0) {
@@ -1091,7 +1127,8 @@ int weno_theta_step_batched(const wt_problem* prob, const wt_segment* segs, int3
     cudaEventDestroy(e1);
     {
       std::lock_guard<std::mutex> lk(g_graph_mu);
-      g_tuned.push_back(TuneEntry{prob->flux, prob->mode, nprob, dev, total, pitch, tile});
+      if (g_tuned.size() >= 256) g_tuned.erase(g_tuned.begin());
+      g_tuned.push_back(TuneEntry{prob->flux, prob->mode, nprob, dev, total, pitch, mix, tile});
     }
     if ((rc = init_ctl()) != WT_OK) return rc;  // the trial launches touched the alpha slots
   }

@@ -17,12 +17,15 @@ struct FluxM {
 
 // Tile geometry: T cells, T + 1 interfaces, m threads per interface (one per field), or with
 // SPLIT = 2 (the step-blocked tiles) a pair of adjacent threads per (interface, field), one
-// per side of the reconstruction (two warps per SMSP where the tile fills one warp per SMSP)
-template <int T, int M, int SPLIT = 1>
+// per side of the reconstruction (two warps per SMSP where the tile fills one warp per SMSP).
+// IPT > 1 (stage and batched tiles): each thread carries IPT (interface, field) items, so the
+// tile has about a 1/IPT of the threads and each thread IPT times the work of every phase.
+template <int T, int M, int SPLIT = 1, int IPT = 1>
 struct Tile1D {
+  static_assert(IPT == 1 || SPLIT == 1, "thread pairs carry one item");
   static constexpr int W = (T + 9) & ~1;              // staged window: T + 6 cells + alignment slack, even
   static constexpr int NI = T + 1;
-  static constexpr int NT = SPLIT * ((M * NI + 31) / 32) * 32;
+  static constexpr int NT = SPLIT * ((M * NI + 32 * IPT - 1) / (32 * IPT)) * 32;
   // shared-memory layout in doubles
   static constexpr int kBar = 0;
   static constexpr int kUin = 2;
@@ -229,7 +232,7 @@ struct AlphaWait {
 // written and then gathered by the last warp while the others go on).  Returns false if a
 // wait for the alphas timed out (the flag word then holds 2) or, at the first stage of a
 // step-blocked RK step, if some CTA has seen a failure (flag word 3): the step is not taken.
-template <class MATH, int FLUX, int STAGE, int T, int MODE>
+template <class MATH, int FLUX, int STAGE, int T, int MODE, int IPT = 1>
 __device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long long js, const int Ts, const int off,
                                                 const long long own_lo, const long long own_hi,
                                                 double (&alpha)[FluxM<FLUX>::m], double& dt, double* sm,
@@ -237,9 +240,10 @@ __device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long
   constexpr int M = FluxM<FLUX>::m;
   // step-blocked tiles split each reconstruction pair over two threads (see phase C1)
   constexpr int SPLIT = (MODE == kStepBlocked) ? 2 : 1;
-  using TL = Tile1D<T, M, SPLIT>;
+  static_assert(IPT == 1 || MODE != kStepBlocked, "the step-blocked tiles carry one item per thread pair");
+  using TL = Tile1D<T, M, SPLIT, IPT>;
   constexpr int W = TL::W, NI = TL::NI, NT = TL::NT;
-  static_assert(NT >= SPLIT * M * NI, "one (interface, field) item per thread (per thread pair with SPLIT = 2)");
+  static_assert(NT * IPT >= SPLIT * M * NI, "IPT (interface, field) items per thread (one per thread pair with SPLIT = 2)");
   double* s_uin = sm + TL::kUin;
   double* s_un = sm + TL::kUn;
   double* s_f = sm + TL::kF;
@@ -445,7 +449,7 @@ __device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long
         pb[5 - h] = __shfl_xor_sync(0xffffffffu, ob[h], 1);
       }
     }
-  } else if (has_item) {
+  } else if (has_item && IPT == 1) {
     if (FLUX == WT_FLUX_EULER1D) {
       double l[3] = {s_L[(3 * s) * NI + i], s_L[(3 * s + 1) * NI + i], s_L[(3 * s + 2) * NI + i]};
 #pragma unroll
@@ -516,7 +520,36 @@ __device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long
       s_F[dst] = MATH::weno(q, a.eps, a.alpha_R);
     }
   };
-  if (has_item) {
+  if constexpr (IPT > 1) {
+    // several items per thread: projection and both reconstructions of each item in turn, with
+    // the operations of the one-item path
+    for (int it2 = tid; it2 < M * ni; it2 += NT) {
+      const int s2 = it2 / ni, i2 = it2 - s2 * ni;
+      double qa[6], qb[6];
+      if (FLUX == WT_FLUX_EULER1D) {
+        double l[3] = {s_L[(3 * s2) * NI + i2], s_L[(3 * s2 + 1) * NI + i2], s_L[(3 * s2 + 2) * NI + i2]};
+#pragma unroll
+        for (int kk = 0; kk < 6; ++kk) {
+          const int k = i2 + kk;
+          double f[3] = {s_f[k], s_f[W + k], s_f[2 * W + k]};
+          double U[3] = {s_uin[off + k], s_uin[W + off + k], s_uin[2 * W + off + k]};
+          MATH::project3_ab(l, f, U, qa[kk], qb[kk]);
+        }
+      } else {
+#pragma unroll
+        for (int kk = 0; kk < 6; ++kk) MATH::project1_ab(s_f[i2 + kk], s_uin[off + i2 + kk], qa[kk], qb[kk]);
+      }
+      const double al = (s2 == 0) ? alpha[0] : ((s2 == 1) ? alpha[1] : alpha[M - 1]);
+      double vp[6], vm[6];
+#pragma unroll
+      for (int kk = 0; kk < 6; ++kk) MATH::project_v(qa[kk], qb[kk], al, vp[kk], vm[kk]);
+      double qm[6];
+#pragma unroll
+      for (int kk = 0; kk < 6; ++kk) qm[kk] = vm[5 - kk];
+      reconstruct(vp, s2 * NI + i2);
+      reconstruct(qm, M * NI + s2 * NI + i2);
+    }
+  } else if (has_item) {
     const double al = (s == 0) ? alpha[0] : ((s == 1) ? alpha[1] : alpha[M - 1]);
     if constexpr (SPLIT == 2) {
       double q[6];
@@ -700,11 +733,11 @@ __device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long
   return true;
 }
 
-template <class MATH, int FLUX, int STAGE, int T>
+template <class MATH, int FLUX, int STAGE, int T, int IPT = 1>
 __device__ __forceinline__ bool stage1d_tile(const Stage1DArgs& a, const long long j0, const bool first_tile, double* sm,
                                              uint32_t& phase) {
   constexpr int M = FluxM<FLUX>::m;
-  using TL = Tile1D<T, M>;
+  using TL = Tile1D<T, M, 1, IPT>;
   constexpr int W = TL::W;
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + TL::kBar);
   double* s_uin = sm + TL::kUin;
@@ -771,8 +804,8 @@ __device__ __forceinline__ bool stage1d_tile(const Stage1DArgs& a, const long lo
     ctl->active = 1;
   }
 
-  stage1d_compute<MATH, FLUX, STAGE, T, kStage>(a, j0, Tc, off, j0, j0 + Tc, alpha, dt, sm,
-                                                AlphaWait{0ull, 0, -1, 0, 0.0, 0.0, 0.0, 0.0});
+  stage1d_compute<MATH, FLUX, STAGE, T, kStage, IPT>(a, j0, Tc, off, j0, j0 + Tc, alpha, dt, sm,
+                                                     AlphaWait{0ull, 0, -1, 0, 0.0, 0.0, 0.0, 0.0});
   if (STAGE != STAGE_RHS) {
     if (STAGE == STAGE_RK3 && first_tile && tid == 0) {
       ctl->t = ctl->t + dt;
@@ -796,9 +829,9 @@ __global__ void __launch_bounds__(Tile1D<T, FluxM<FLUX>::m>::NT) stage1d_kernel(
 
 // Batched stage: a persistent grid walks a table of (problem, tile) work items over many
 // independent problems, each with its own grid, boundary conditions, alphas and dt.
-template <class MATH, int FLUX, int STAGE, int T>
-__global__ void __launch_bounds__(Tile1D<T, FluxM<FLUX>::m>::NT) stage1d_batched_kernel(const BatchArgs b) {
-  using TL = Tile1D<T, FluxM<FLUX>::m>;
+template <class MATH, int FLUX, int STAGE, int T, int IPT>
+__global__ void __launch_bounds__(Tile1D<T, FluxM<FLUX>::m, 1, IPT>::NT) stage1d_batched_kernel(const BatchArgs b) {
+  using TL = Tile1D<T, FluxM<FLUX>::m, 1, IPT>;
   extern __shared__ __align__(16) double sm[];
   pdl_launch_dependents();
   if (threadIdx.x == 0) mbar_init(reinterpret_cast<uint64_t*>(sm + TL::kBar), 1);
@@ -826,7 +859,7 @@ __global__ void __launch_bounds__(Tile1D<T, FluxM<FLUX>::m>::NT) stage1d_batched
     a.bc_hi = sg.bc_hi;
     a.ctl = b.ctl + item.x;
     const long long j0 = (long long)item.y * T;
-    if (!stage1d_tile<MATH, FLUX, STAGE, T>(a, j0, j0 == 0, sm, phase)) return;
+    if (!stage1d_tile<MATH, FLUX, STAGE, T, IPT>(a, j0, j0 == 0, sm, phase)) return;
     __syncthreads();
   }
 }
@@ -1318,22 +1351,24 @@ cudaError_t launch_alpha1d_policy(int flux, const double* u, long long n, long l
   return cudaGetLastError();
 }
 
-template <class MATH, int FLUX, int STAGE, int T>
+template <class MATH, int FLUX, int STAGE, int T, int IPT>
 cudaError_t launch_stage1d_batched_t(const BatchArgs& b, int grid, cudaStream_t st) {
-  using TL = Tile1D<T, FluxM<FLUX>::m>;
-  return launch_pdl(stage1d_batched_kernel<MATH, FLUX, STAGE, T>, dim3(grid), dim3(TL::NT), TL::bytes, st, b);
+  using TL = Tile1D<T, FluxM<FLUX>::m, 1, IPT>;
+  static_assert(TL::bytes <= 48 * 1024, "tile exceeds the default dynamic shared memory limit");
+  return launch_pdl(stage1d_batched_kernel<MATH, FLUX, STAGE, T, IPT>, dim3(grid), dim3(TL::NT), TL::bytes, st, b);
 }
 
-template <class MATH, int FLUX, int T>
+template <class MATH, int FLUX, int T, int IPT = 1>
 cudaError_t launch_stage1d_batched_flux(int stage, const BatchArgs& b, int grid, cudaStream_t st) {
   switch (stage) {
-    case STAGE_RK1: return launch_stage1d_batched_t<MATH, FLUX, STAGE_RK1, T>(b, grid, st);
-    case STAGE_RK2: return launch_stage1d_batched_t<MATH, FLUX, STAGE_RK2, T>(b, grid, st);
-    case STAGE_RK3: return launch_stage1d_batched_t<MATH, FLUX, STAGE_RK3, T>(b, grid, st);
+    case STAGE_RK1: return launch_stage1d_batched_t<MATH, FLUX, STAGE_RK1, T, IPT>(b, grid, st);
+    case STAGE_RK2: return launch_stage1d_batched_t<MATH, FLUX, STAGE_RK2, T, IPT>(b, grid, st);
+    case STAGE_RK3: return launch_stage1d_batched_t<MATH, FLUX, STAGE_RK3, T, IPT>(b, grid, st);
   }
   return cudaErrorInvalidValue;
 }
 
+// tile: the batched tile code, cells per tile + 1000 x (items per thread - 1) (wt_launch.h)
 template <class MATH>
 cudaError_t launch_stage1d_batched_policy(int flux, int stage, int tile, const BatchArgs& b, int grid,
                                           cudaStream_t st) {
@@ -1341,6 +1376,11 @@ cudaError_t launch_stage1d_batched_policy(int flux, int stage, int tile, const B
     if (tile == 31) return launch_stage1d_batched_flux<MATH, WT_FLUX_EULER1D, 31>(stage, b, grid, st);
     if (tile == 63) return launch_stage1d_batched_flux<MATH, WT_FLUX_EULER1D, 63>(stage, b, grid, st);
     if (tile == 127) return launch_stage1d_batched_flux<MATH, WT_FLUX_EULER1D, 127>(stage, b, grid, st);
+    if (tile == 1063) return launch_stage1d_batched_flux<MATH, WT_FLUX_EULER1D, 63, 2>(stage, b, grid, st);
+    if (tile == 1127) return launch_stage1d_batched_flux<MATH, WT_FLUX_EULER1D, 127, 2>(stage, b, grid, st);
+    if (tile == 2127) return launch_stage1d_batched_flux<MATH, WT_FLUX_EULER1D, 127, 3>(stage, b, grid, st);
+    if (tile == 3127) return launch_stage1d_batched_flux<MATH, WT_FLUX_EULER1D, 127, 4>(stage, b, grid, st);
+    if (tile == 5127) return launch_stage1d_batched_flux<MATH, WT_FLUX_EULER1D, 127, 6>(stage, b, grid, st);
   } else if (flux == WT_FLUX_ADVECTION) {
     if (tile == 63) return launch_stage1d_batched_flux<MATH, WT_FLUX_ADVECTION, 63>(stage, b, grid, st);
     if (tile == 127) return launch_stage1d_batched_flux<MATH, WT_FLUX_ADVECTION, 127>(stage, b, grid, st);
@@ -1351,12 +1391,12 @@ cudaError_t launch_stage1d_batched_policy(int flux, int stage, int tile, const B
   return cudaErrorInvalidValue;
 }
 
-template <class MATH, int FLUX, int T>
+template <class MATH, int FLUX, int T, int IPT = 1>
 int batched_occupancy_t() {
-  using TL = Tile1D<T, FluxM<FLUX>::m>;
+  using TL = Tile1D<T, FluxM<FLUX>::m, 1, IPT>;
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, stage1d_batched_kernel<MATH, FLUX, STAGE_RK2, T>, TL::NT,
-                                                    TL::bytes) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, stage1d_batched_kernel<MATH, FLUX, STAGE_RK2, T, IPT>,
+                                                    TL::NT, TL::bytes) != cudaSuccess)
     return 0;
   return nb;
 }
@@ -1367,6 +1407,11 @@ int batched_occupancy_policy(int flux, int tile) {
     if (tile == 31) return batched_occupancy_t<MATH, WT_FLUX_EULER1D, 31>();
     if (tile == 63) return batched_occupancy_t<MATH, WT_FLUX_EULER1D, 63>();
     if (tile == 127) return batched_occupancy_t<MATH, WT_FLUX_EULER1D, 127>();
+    if (tile == 1063) return batched_occupancy_t<MATH, WT_FLUX_EULER1D, 63, 2>();
+    if (tile == 1127) return batched_occupancy_t<MATH, WT_FLUX_EULER1D, 127, 2>();
+    if (tile == 2127) return batched_occupancy_t<MATH, WT_FLUX_EULER1D, 127, 3>();
+    if (tile == 3127) return batched_occupancy_t<MATH, WT_FLUX_EULER1D, 127, 4>();
+    if (tile == 5127) return batched_occupancy_t<MATH, WT_FLUX_EULER1D, 127, 6>();
   } else if (flux == WT_FLUX_ADVECTION) {
     if (tile == 63) return batched_occupancy_t<MATH, WT_FLUX_ADVECTION, 63>();
     if (tile == 127) return batched_occupancy_t<MATH, WT_FLUX_ADVECTION, 127>();

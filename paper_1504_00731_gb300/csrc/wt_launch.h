@@ -59,6 +59,9 @@ struct BatchArgs {
   double gamma, adv_speed, eps, alpha_R;
 };
 
+// tile: a tile code, cells per tile + 1000 x (items per thread - 1): 31, 63, 127 (Euler; 63, 127
+// scalar) with one (interface, field) item per thread, 1063 and 1127 (Euler) with two,
+// 2127, 3127 and 5127 (Euler) with three, four and six
 cudaError_t launch_stage1d_batched_strict(int flux, int stage, int tile, const BatchArgs& b, int grid, cudaStream_t st);
 cudaError_t launch_stage1d_batched_fast(int flux, int stage, int tile, const BatchArgs& b, int grid, cudaStream_t st);
 // resident CTAs per SM of the batched stage kernel (occupancy), 0 on error

@@ -79,6 +79,32 @@ def test_batched_fast_equals_single_problem_runs(wtlib):
         assert np.array_equal(us.cpu().numpy(), u[:, o:o + n]), p
 
 
+@pytest.mark.parametrize("code", [31, 63, 127, 1063, 1127, 2127, 3127, 5127])
+def test_every_autotuner_candidate_gives_the_same_bits(wtlib, oracle, code, monkeypatch):
+    """Each (tile, items per thread) candidate the autotuner may pick, fixed through
+    WT_BATCHED_TILE: strict mode equals the oracle bit for bit problem by problem, and fast mode
+    equals the single-problem runs bit for bit."""
+    b, O = wtlib, oracle
+    monkeypatch.setenv("WT_BATCHED_TILE", str(code))
+    batch = W.euler_batch(len(EDGE_LENGTHS), seed=4, lengths=EDGE_LENGTHS)
+    prob = b.problem(b.WT_FLUX_EULER1D, mode=b.WT_MODE_STRICT, alpha_R=W.ALPHA_R_SEEDED)
+    u, t = _run_batched(b, prob, batch, 6)
+    for p in range(len(EDGE_LENGTHS)):
+        ref, t_ref, _ = _oracle_one(O, batch, p, 6)
+        o, n = int(batch.offsets[p]), int(batch.lengths[p])
+        assert t[p] == t_ref and np.array_equal(u[:, o:o + n], ref), (code, p, n)
+    fast = b.problem(b.WT_FLUX_EULER1D, mode=b.WT_MODE_FAST, alpha_R=W.ALPHA_R_SEEDED)
+    uf, tf = _run_batched(b, fast, batch, 6)
+    for p in range(len(EDGE_LENGTHS)):
+        o, n = int(batch.offsets[p]), int(batch.lengths[p])
+        pb = b.problem(b.WT_FLUX_EULER1D, bc=int(batch.bc[p]), mode=b.WT_MODE_FAST, alpha_R=W.ALPHA_R_SEEDED)
+        g = b.grid_1d(n, -5.0, 5.0)
+        ws = b.alloc_workspace(b.workspace_bytes(pb, g))
+        us = torch.from_numpy(np.ascontiguousarray(batch.u[:, o:o + n])).cuda()
+        ts, _ = b.weno_theta_step(pb, g, us, 0.5, ws, max_steps=6)
+        assert ts == tf[p] and np.array_equal(us.cpu().numpy(), uf[:, o:o + n]), (code, p, n)
+
+
 def test_batched_scalar_strict_and_host_arrays(wtlib, oracle):
     b, O = wtlib, oracle
     lengths = [3, 40, 64, 65, 200, 333]
