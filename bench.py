@@ -71,6 +71,7 @@ COUNTERS = {
     "batched": os.path.join(ROOT, "profiles", "stage1d_batched_euler_counters.json"),
     "stepblock": os.path.join(ROOT, "profiles", "stepblock1d_euler_N4096_counters.json"),
     "stage2d": os.path.join(ROOT, "profiles", "stage2d_euler_counters.json"),
+    "adjoint": os.path.join(ROOT, "profiles", "adj_stage_euler_counters.json"),
 }
 
 
@@ -714,8 +715,10 @@ def run_profile_case(name):
     BLD.build_library()
     dev = torch.device("cuda", 0)
     if name == "batched-512":
-        # 512 problems of the batched workload (6.9 M cells, 165 MB per state, above L2): the
-        # autotuning call, then one RK step (its three stage launches are the ones to capture)
+        # 512 problems of the batched workload (6.9 M cells, 165 MB per state, above L2), with the
+        # tile the autotuner picks on the whole batch (127 cells, six items per thread): two calls
+        # of one RK step, three stage launches each (the second call's are the ones to capture)
+        os.environ.setdefault("WT_BATCHED_TILE", "5127")
         b = W.euler_batch(512, seed=0)
         prob = B.problem(B.WT_FLUX_EULER1D, mode=B.WT_MODE_FAST, alpha_R=W.ALPHA_R_SEEDED)
         segs = segments(B, b)

@@ -195,6 +195,9 @@ int weno_theta_step_batched(const wt_problem* prob, const wt_segment* segs, int3
  *   dJ_du0  [nprob][3][n] out: gradient with respect to u(0)
  *   uT      [nprob][3][n] out (may be NULL): u(T)
  * prob->flux must be WT_FLUX_EULER1D.  ws must hold wt_adjoint_workspace_bytes(...) bytes.
+ * The environment variable WT_ADJ_TILE (31, 2031, 63, 1063 or 2063: cells per reverse tile +
+ * 1000 x (items per thread - 1)) overrides the reverse kernel's tile; the gradients agree to
+ * rounding.
  * Synchronises `stream`.
  */
 size_t wt_adjoint_workspace_bytes(const wt_problem* prob, const wt_grid* grid, int32_t nprob, int64_t n_steps,

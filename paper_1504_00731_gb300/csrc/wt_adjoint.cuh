@@ -220,12 +220,14 @@ __device__ __forceinline__ void roe_reverse(const double* Ua, const double* Ub, 
 // Reverse stage over one tile
 // ---------------------------------------------------------------------------------------
 
-template <int T>
+// T cells per tile; IPT (interface, field) items per thread in the per-item phase, so the
+// tile has about a 1/IPT of the threads (every phase loops over its items)
+template <int T, int IPT = 1>
 struct AdjTile {
   static constexpr int M = 3;
   static constexpr int W = (T + 9) & ~1;
   static constexpr int NI = T + 1;
-  static constexpr int NT = ((M * NI + 31) / 32) * 32;
+  static constexpr int NT = ((M * NI + 32 * IPT - 1) / (32 * IPT)) * 32;
   static constexpr int kBar = 0;
   static constexpr int kUin = 2;
   static constexpr int kF = kUin + M * W;
@@ -259,9 +261,9 @@ __device__ __forceinline__ double block_sum_to(double v, double* scratch, int k)
   return s;
 }
 
-template <class MATH, int T>
-__global__ void __launch_bounds__(AdjTile<T>::NT) adj_stage_kernel(const AdjArgs a) {
-  using TL = AdjTile<T>;
+template <class MATH, int T, int IPT>
+__global__ void __launch_bounds__(AdjTile<T, IPT>::NT) adj_stage_kernel(const AdjArgs a) {
+  using TL = AdjTile<T, IPT>;
   constexpr int W = TL::W, NI = TL::NI, NT = TL::NT;
   extern __shared__ __align__(16) double sm[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + TL::kBar);
@@ -653,26 +655,38 @@ __global__ void adj_record_kernel(const Ctl* ctl, int slot, double* alpha_out, d
 #endif  // WT_ADJOINT_COMMON_KERNELS
 
 // grid <= 0: as many CTAs as can be resident (persistent loop over the tile table)
-template <class MATH>
-cudaError_t launch_adj_stage_policy(const AdjArgs& a, int grid, cudaStream_t st) {
-  constexpr int T = 31;
-  using TL = AdjTile<T>;
+template <class MATH, int T, int IPT>
+cudaError_t launch_adj_stage_t(const AdjArgs& a, int grid, cudaStream_t st) {
+  using TL = AdjTile<T, IPT>;
+  static_assert(TL::bytes <= 48 * 1024, "tile exceeds the default dynamic shared memory limit");
   if (grid <= 0) {
     int dev = 0, sms = 0, nb = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, adj_stage_kernel<MATH, T>, TL::NT, TL::bytes);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, adj_stage_kernel<MATH, T, IPT>, TL::NT, TL::bytes);
     long long g = (long long)(nb > 0 ? nb : 1) * (sms > 0 ? sms : 1);
     grid = (int)(g < a.ntiles ? g : a.ntiles);
   }
-  adj_stage_kernel<MATH, T><<<grid, TL::NT, TL::bytes, st>>>(a);
+  adj_stage_kernel<MATH, T, IPT><<<grid, TL::NT, TL::bytes, st>>>(a);
   return cudaGetLastError();
+}
+
+// code: cells per reverse tile + 1000 x (items per thread - 1) (adj_tile_code)
+template <class MATH>
+cudaError_t launch_adj_stage_policy(const AdjArgs& a, int grid, int code, cudaStream_t st) {
+  switch (code) {
+    case 31: return launch_adj_stage_t<MATH, 31, 1>(a, grid, st);
+    case 2031: return launch_adj_stage_t<MATH, 31, 3>(a, grid, st);
+    case 63: return launch_adj_stage_t<MATH, 63, 1>(a, grid, st);
+    case 1063: return launch_adj_stage_t<MATH, 63, 2>(a, grid, st);
+    case 2063: return launch_adj_stage_t<MATH, 63, 3>(a, grid, st);
+  }
+  return cudaErrorInvalidValue;
 }
 
 template <class MATH>
 cudaError_t prepare_adj_policy() {
-  using TL = AdjTile<31>;
-  return cudaFuncSetAttribute(adj_stage_kernel<MATH, 31>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TL::bytes);
+  return cudaSuccess;  // every reverse tile fits the default 48 KB of dynamic shared memory
 }
 
 template <class MATH>

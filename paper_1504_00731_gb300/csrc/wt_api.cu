@@ -1244,8 +1244,9 @@ int weno_theta_adjoint(const wt_problem* prob, const wt_grid* grid, int32_t npro
   double* stage_buf = reinterpret_cast<double*>(w + lay.staging);
   auto segu = [&](int64_t k, int s) { return segU + ((size_t)k * 3 + s) * 3 * (size_t)P; };
 
-  // ---- problems, tiles (forward T = 127, reverse T = adj_tile_width(), problem-major)
-  const int Tr = adj_tile_width();
+  // ---- problems, tiles (forward T = 127, reverse T from the reverse tile code, problem-major)
+  const int adj_code = adj_tile_code();
+  const int Tr = adj_code % 1000;
   std::vector<BatchSeg> hs(nprob);
   std::vector<long long> hgoff(nprob);
   std::vector<int> hts(nprob), htc(nprob);
@@ -1312,7 +1313,10 @@ int weno_theta_adjoint(const wt_problem* prob, const wt_grid* grid, int32_t npro
   };
   const int nf = (int)tf.size(), nr = (int)tr.size();
   (void)nr;
-  const int grid_f = batched_grid_size(prob, 127, nf, dev);
+  // the forward stages: 127-cell tiles with six (interface, field) items per thread, the
+  // batched autotuner's pick on large Euler batches (every tile code gives the same bits)
+  constexpr int kFwdTile = 5127;
+  const int grid_f = batched_grid_size(prob, kFwdTile, nf, dev);
 
   // Steps of one segment from segu(0, 0), keeping u^n, u^(1), u^(2) of every step and the
   // alphas and dt each stage used; the last step's u^{n+1} goes to final_out (if not null).
@@ -1320,12 +1324,12 @@ int weno_theta_adjoint(const wt_problem* prob, const wt_grid* grid, int32_t npro
     for (int64_t k = 0; k < kseg; ++k) {
       double* ra = rec_a + (size_t)k * 3 * 4 * nprob;
       WT_CUDA(launch_adj_record(ctl, 0, ra, nullptr, nprob, st));
-      WT_CUDA(launch_batched_stage(prob, STAGE_RK1, 127, bargs(segu(k, 0), nullptr, segu(k, 1), tiles_f, nf), grid_f, st));
+      WT_CUDA(launch_batched_stage(prob, STAGE_RK1, kFwdTile, bargs(segu(k, 0), nullptr, segu(k, 1), tiles_f, nf), grid_f, st));
       WT_CUDA(launch_adj_record(ctl, 1, ra + 4 * nprob, rec_dt + (size_t)k * nprob, nprob, st));
-      WT_CUDA(launch_batched_stage(prob, STAGE_RK2, 127, bargs(segu(k, 1), segu(k, 0), segu(k, 2), tiles_f, nf), grid_f, st));
+      WT_CUDA(launch_batched_stage(prob, STAGE_RK2, kFwdTile, bargs(segu(k, 1), segu(k, 0), segu(k, 2), tiles_f, nf), grid_f, st));
       WT_CUDA(launch_adj_record(ctl, 2, ra + 8 * nprob, nullptr, nprob, st));
       double* out = (k + 1 < kseg) ? segu(k + 1, 0) : final_out;
-      if (out) WT_CUDA(launch_batched_stage(prob, STAGE_RK3, 127, bargs(segu(k, 2), segu(k, 0), out, tiles_f, nf), grid_f, st));
+      if (out) WT_CUDA(launch_batched_stage(prob, STAGE_RK3, kFwdTile, bargs(segu(k, 2), segu(k, 0), out, tiles_f, nf), grid_f, st));
     }
     return WT_OK;
   };
@@ -1407,7 +1411,7 @@ int weno_theta_adjoint(const wt_problem* prob, const wt_grid* grid, int32_t npro
         aa.goff = goff;
         aa.G = Gbuf;
         aa.partial = partial;
-        WT_CUDA(strict ? launch_adj_stage_strict(aa, grid_r, st) : launch_adj_stage_fast(aa, grid_r, st));
+        WT_CUDA(strict ? launch_adj_stage_strict(aa, grid_r, adj_code, st) : launch_adj_stage_fast(aa, grid_r, adj_code, st));
         GatherArgs ga;
         memset(&ga, 0, sizeof ga);
         ga.uin = in;

@@ -1,6 +1,8 @@
 // Fast-arithmetic instantiations of the 1D kernels, plus the boundary-fill (pack) and
 // unpack kernels, which do no arithmetic.
 #define WT_ADJOINT_COMMON_KERNELS
+#include <cstdlib>
+
 #include "wt_kernels.cuh"
 #include "wt_kernels2d.cuh"
 #include "wt_adjoint.cuh"
@@ -218,8 +220,8 @@ cudaError_t launch_alpha2d_fast(const double* u, long long nx, long long ny, lon
 
 cudaError_t prepare_adj_fast() { return prepare_adj_policy<FastMath>(); }
 
-cudaError_t launch_adj_stage_fast(const AdjArgs& a, int grid, cudaStream_t st) {
-  return launch_adj_stage_policy<FastMath>(a, grid, st);
+cudaError_t launch_adj_stage_fast(const AdjArgs& a, int grid, int code, cudaStream_t st) {
+  return launch_adj_stage_policy<FastMath>(a, grid, code, st);
 }
 
 cudaError_t launch_adj_argmax_fast(const double* uin, long long pitch, const BatchSeg* segs, int nprob,
@@ -227,7 +229,17 @@ cudaError_t launch_adj_argmax_fast(const double* uin, long long pitch, const Bat
   return launch_adj_argmax_policy<FastMath>(uin, pitch, segs, nprob, maxn, alpha, gamma, arg, st);
 }
 
-int adj_tile_width() { return 31; }
+// The reverse tile: 63 cells with three (interface, field) items per thread (64 threads), the
+// fastest of the compiled codes on the adjoint workload, unless WT_ADJ_TILE names another (31,
+// 2031, 63, 1063, 2063).  The gradients agree to rounding: the per-tile partial sums of the
+// alpha and dt derivatives are added in another order.
+int adj_tile_code() {
+  if (const char* e = getenv("WT_ADJ_TILE")) {
+    const int c = atoi(e);
+    if (c == 31 || c == 2031 || c == 63 || c == 1063 || c == 2063) return c;
+  }
+  return 2063;
+}
 
 cudaError_t launch_adj_gather(const GatherArgs& a, int nprob, long long maxn, cudaStream_t st) {
   long long bx = (maxn + 255) / 256;

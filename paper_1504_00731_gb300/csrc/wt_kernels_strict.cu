@@ -52,8 +52,8 @@ cudaError_t launch_alpha2d_strict(const double* u, long long nx, long long ny, l
 
 cudaError_t prepare_adj_strict() { return prepare_adj_policy<StrictMath>(); }
 
-cudaError_t launch_adj_stage_strict(const AdjArgs& a, int grid, cudaStream_t st) {
-  return launch_adj_stage_policy<StrictMath>(a, grid, st);
+cudaError_t launch_adj_stage_strict(const AdjArgs& a, int grid, int code, cudaStream_t st) {
+  return launch_adj_stage_policy<StrictMath>(a, grid, code, st);
 }
 
 cudaError_t launch_adj_argmax_strict(const double* uin, long long pitch, const BatchSeg* segs, int nprob,

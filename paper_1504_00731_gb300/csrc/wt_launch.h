@@ -145,8 +145,9 @@ struct GatherArgs {  // per-cell gather of the interface contributions
 
 cudaError_t prepare_adj_strict();
 cudaError_t prepare_adj_fast();
-cudaError_t launch_adj_stage_strict(const AdjArgs& a, int grid, cudaStream_t st);
-cudaError_t launch_adj_stage_fast(const AdjArgs& a, int grid, cudaStream_t st);
+// code: the reverse tile, cells + 1000 x (items per thread - 1) (adj_tile_code)
+cudaError_t launch_adj_stage_strict(const AdjArgs& a, int grid, int code, cudaStream_t st);
+cudaError_t launch_adj_stage_fast(const AdjArgs& a, int grid, int code, cudaStream_t st);
 cudaError_t launch_adj_argmax_strict(const double* uin, long long pitch, const BatchSeg* segs, int nprob,
                                      long long maxn, const double* alpha, double gamma, int* arg, cudaStream_t st);
 cudaError_t launch_adj_argmax_fast(const double* uin, long long pitch, const BatchSeg* segs, int nprob, long long maxn,
@@ -157,7 +158,7 @@ cudaError_t launch_adj_apply(const double* uin, long long pitch, const BatchSeg*
                              const int* arg, double* ubar, long long ustride, double* dtbar, int final_stage,
                              double gamma, int nprob, cudaStream_t st);
 cudaError_t launch_adj_record(const Ctl* ctl, int slot, double* alpha_out, double* dt_out, int nprob, cudaStream_t st);
-int adj_tile_width();
+int adj_tile_code();
 
 cudaError_t launch_selftest_wait(int which, unsigned long long* word, unsigned long long* mbox, long long limit,
                                  int* result, cudaStream_t st);
