@@ -336,14 +336,23 @@ __global__ void __launch_bounds__(AdjTile<T, IPT>::NT) adj_stage_kernel(const Ad
       s_sr[k] = sr;
     }
     __syncthreads();
-    // ---- C0: Roe per interface (local li: cells li+2 | li+3; global interface j0 - 1 + li)
+    // ---- C0: per interface (local li: cells li+2 | li+3; global interface j0 - 1 + li, record
+    //      slot j0 + li), from the forward stage's record: the eigenvectors rebuilt from Roe's
+    //      mean state exactly as the forward formed them, F_s = F+_s + F-_s and the branch flags
+    const double* recp = a.rec + (size_t)a.goff[p] * kAdjRec;
+    unsigned* s_flags = reinterpret_cast<unsigned*>(s_red);  // free until the tile sums of phase E
+    static_assert(NI <= 4 * 32 * 2, "one flags word per interface in the reduction buffer");
     for (int i = tid; i < ni; i += NT) {
+      const double* r = recp + (size_t)(j0 + i) * kAdjRec;
       double L[9], rs[3];
-      MATH::roe(s_sr[i + 2], s_vel[i + 2], s_H[i + 2], s_sr[i + 3], s_vel[i + 3], s_H[i + 3], a.gamma, L, rs);
+      MATH::roe_mean(r[0], r[1], a.gamma, L, rs);
 #pragma unroll
       for (int e = 0; e < 9; ++e) s_L[e * NI + i] = L[e];
 #pragma unroll
       for (int e = 0; e < 3; ++e) s_rs[e * NI + i] = rs[e];
+#pragma unroll
+      for (int e = 0; e < 3; ++e) s_F[e * NI + i] = r[2 + e];
+      s_flags[i] = (unsigned)__double_as_longlong(r[5]);
     }
     __syncthreads();
     // ---- hbar per interface: L_gi and L_gi+1 depend on h of interface gi = j0 - 1 + i
@@ -355,29 +364,41 @@ __global__ void __launch_bounds__(AdjTile<T, IPT>::NT) adj_stage_kernel(const Ad
       s_hb[c * NI + i] = (wr - wl) * sg.inv_dx;
     }
     __syncthreads();
-    // ---- C1: per (interface, field), one pass: projection, both reconstructions with the
-    //      forward policy's branches, F_s; then their reverse (owned interfaces only)
+    // ---- C1: per (interface, field) of the owned interfaces: the reverse of both
+    //      reconstructions with the forward's branches (a restricted stencil's gradient is a
+    //      fixed coefficient vector; only the others need the projected stencil values, taken
+    //      with the forward's operations), of the Lax-Friedrichs split and of the projection
     double abar0 = 0.0, abar1 = 0.0, abar2 = 0.0;
     for (int item2 = tid; item2 < 3 * ni; item2 += NT) {
       const int s = item2 / ni, i = item2 - s * ni;
-      const double l[3] = {s_L[(3 * s) * NI + i], s_L[(3 * s + 1) * NI + i], s_L[(3 * s + 2) * NI + i]};
-      double vp[6], vm[6], qm[6], pb[6];
-#pragma unroll
-      for (int kk = 0; kk < 6; ++kk) {
-        const int k = i + kk;
-        const double f[3] = {s_f[k], s_f[W + k], s_f[2 * W + k]};
-        const double U[3] = {s_uin[off + k], s_uin[W + off + k], s_uin[2 * W + off + k]};
-        double pa;
-        MATH::project3_ab(l, f, U, pa, pb[kk]);  // the same operations as project3
-        MATH::project_v(pa, pb[kk], al[s], vp[kk], vm[kk]);
-      }
-#pragma unroll
-      for (int kk = 0; kk < 6; ++kk) qm[kk] = vm[5 - kk];
-      bool rp, tp, rm, tm;
-      const double Fs = MATH::weno_flags(vp, a.eps, a.alpha_R, rp, tp) + MATH::weno_flags(qm, a.eps, a.alpha_R, rm, tm);
-      s_F[s * NI + i] = Fs;
       const bool owned = (i >= 1) || (j0 == 0);
       if (!owned) continue;
+      const double l[3] = {s_L[(3 * s) * NI + i], s_L[(3 * s + 1) * NI + i], s_L[(3 * s + 2) * NI + i]};
+      const unsigned fl = s_flags[i];
+      const bool rp = (fl >> (2 * s)) & 1u, tp = (fl >> (2 * s + 1)) & 1u;
+      const bool rm = (fl >> (2 * (3 + s))) & 1u, tm = (fl >> (2 * (3 + s) + 1)) & 1u;
+      double vp[6] = {0, 0, 0, 0, 0, 0}, qm[6] = {0, 0, 0, 0, 0, 0}, pb[6];
+      if (rp && rm) {
+#pragma unroll
+        for (int kk = 0; kk < 6; ++kk) {
+          const int k = i + kk;
+          const double U[3] = {s_uin[off + k], s_uin[W + off + k], s_uin[2 * W + off + k]};
+          pb[kk] = MATH::project3_b(l, U);
+        }
+      } else {
+        double vm[6];
+#pragma unroll
+        for (int kk = 0; kk < 6; ++kk) {
+          const int k = i + kk;
+          const double f[3] = {s_f[k], s_f[W + k], s_f[2 * W + k]};
+          const double U[3] = {s_uin[off + k], s_uin[W + off + k], s_uin[2 * W + off + k]};
+          double pa;
+          MATH::project3_ab(l, f, U, pa, pb[kk]);  // the same operations as project3
+          MATH::project_v(pa, pb[kk], al[s], vp[kk], vm[kk]);
+        }
+#pragma unroll
+        for (int kk = 0; kk < 6; ++kk) qm[kk] = vm[5 - kk];
+      }
       double* Gs = s_G + (s * NI + i) * 12;
       double* Lbs = s_Lb + (s * NI + i) * 3;
       const double u = s_rs[i], H = s_rs[NI + i], c = s_rs[2 * NI + i];

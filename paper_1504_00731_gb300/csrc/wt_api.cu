@@ -695,8 +695,8 @@ int step_2d(const wt_problem* prob, const wt_grid* grid, double* u, double cfl, 
 // --- discrete adjoint ----------------------------------------------------------------------
 
 struct AdjLayout {
-  size_t ctl, segs, tiles_f, tiles_r, tstart, tcount, goff, un, u1, u2, ckpt, segu, rec_a, rec_dt, v[4], G, partial,
-      arg, dtbar, staging, total;
+  size_t ctl, segs, tiles_f, tiles_r, tstart, tcount, goff, un, u1, u2, ckpt, segu, rec_a, rec_dt, rec, v[4], G,
+      partial, arg, dtbar, staging, total;
   long long pitch;
 };
 
@@ -740,6 +740,8 @@ int adjoint_layout(const wt_problem* prob, const wt_grid* grid, int nprob, int64
   L.segu = take(plane * 3 * (size_t)Kseg);
   L.rec_a = take(sizeof(double) * 12 * nprob * (size_t)Kseg);
   L.rec_dt = take(sizeof(double) * nprob * (size_t)Kseg);
+  // the recording forward pass's per-interface records of every stage of a segment
+  L.rec = take(sizeof(double) * kAdjRec * (size_t)(n + 1) * nprob * 3 * (size_t)Kseg);
   for (int i = 0; i < 4; ++i) L.v[i] = take(vec);
   L.G = take(sizeof(double) * 36 * (size_t)(n + 1) * nprob);
   L.partial = take(sizeof(double) * 4 * (size_t)ntr);
@@ -1238,6 +1240,9 @@ int weno_theta_adjoint(const wt_problem* prob, const wt_grid* grid, int32_t npro
   double* vW = reinterpret_cast<double*>(w + lay.v[2]);
   double* vZ = reinterpret_cast<double*>(w + lay.v[3]);
   double* Gbuf = reinterpret_cast<double*>(w + lay.G);
+  double* recbuf = reinterpret_cast<double*>(w + lay.rec);
+  const size_t rec_stage = (size_t)kAdjRec * (size_t)(n + 1) * nprob;  // doubles per stage's records
+  auto recs = [&](int64_t k, int s) { return recbuf + ((size_t)k * 3 + s) * rec_stage; };
   double* partial = reinterpret_cast<double*>(w + lay.partial);
   int* arg = reinterpret_cast<int*>(w + lay.arg);
   double* dtbar = reinterpret_cast<double*>(w + lay.dtbar);
@@ -1294,9 +1299,11 @@ int weno_theta_adjoint(const wt_problem* prob, const wt_grid* grid, int32_t npro
     return WT_OK;
   };
   if ((rc = init_ctl(Un)) != WT_OK) return rc;
-  auto bargs = [&](const double* in, const double* unp, double* out, const int2* tl, int nt) {
+  auto bargs = [&](const double* in, const double* unp, double* out, const int2* tl, int nt, double* rec = nullptr) {
     BatchArgs b;
     memset(&b, 0, sizeof b);
+    b.rec = rec;
+    b.rec_off = rec ? goff : nullptr;
     b.uin = in;
     b.un = unp;
     b.uout = out;
@@ -1317,6 +1324,10 @@ int weno_theta_adjoint(const wt_problem* prob, const wt_grid* grid, int32_t npro
   // batched autotuner's pick on large Euler batches (every tile code gives the same bits)
   constexpr int kFwdTile = 5127;
   const int grid_f = batched_grid_size(prob, kFwdTile, nf, dev);
+  auto launch_rec_stage = [&](int stage, const BatchArgs& b) {
+    return strict ? launch_stage1d_batched_record_strict(stage, b, grid_f, st)
+                  : launch_stage1d_batched_record_fast(stage, b, grid_f, st);
+  };
 
   // Steps of one segment from segu(0, 0), keeping u^n, u^(1), u^(2) of every step and the
   // alphas and dt each stage used; the last step's u^{n+1} goes to final_out (if not null).
@@ -1324,12 +1335,15 @@ int weno_theta_adjoint(const wt_problem* prob, const wt_grid* grid, int32_t npro
     for (int64_t k = 0; k < kseg; ++k) {
       double* ra = rec_a + (size_t)k * 3 * 4 * nprob;
       WT_CUDA(launch_adj_record(ctl, 0, ra, nullptr, nprob, st));
-      WT_CUDA(launch_batched_stage(prob, STAGE_RK1, kFwdTile, bargs(segu(k, 0), nullptr, segu(k, 1), tiles_f, nf), grid_f, st));
+      WT_CUDA(launch_rec_stage(STAGE_RK1, bargs(segu(k, 0), nullptr, segu(k, 1), tiles_f, nf, recs(k, 0))));
       WT_CUDA(launch_adj_record(ctl, 1, ra + 4 * nprob, rec_dt + (size_t)k * nprob, nprob, st));
-      WT_CUDA(launch_batched_stage(prob, STAGE_RK2, kFwdTile, bargs(segu(k, 1), segu(k, 0), segu(k, 2), tiles_f, nf), grid_f, st));
+      WT_CUDA(launch_rec_stage(STAGE_RK2, bargs(segu(k, 1), segu(k, 0), segu(k, 2), tiles_f, nf, recs(k, 1))));
       WT_CUDA(launch_adj_record(ctl, 2, ra + 8 * nprob, nullptr, nprob, st));
       double* out = (k + 1 < kseg) ? segu(k + 1, 0) : final_out;
-      if (out) WT_CUDA(launch_batched_stage(prob, STAGE_RK3, kFwdTile, bargs(segu(k, 2), segu(k, 0), out, tiles_f, nf), grid_f, st));
+      // stage 3 of a segment's last step runs even where its state is not needed (it is the next
+      // checkpoint, already known): the reverse needs its records.  Its state then goes to U1,
+      // which nothing reads during the reverse sweep.
+      WT_CUDA(launch_rec_stage(STAGE_RK3, bargs(segu(k, 2), segu(k, 0), out ? out : U1, tiles_f, nf, recs(k, 2))));
     }
     return WT_OK;
   };
@@ -1342,7 +1356,7 @@ int weno_theta_adjoint(const wt_problem* prob, const wt_grid* grid, int32_t npro
   {
     BatchArgs a3[3] = {bargs(Un, nullptr, U1, tiles_f, nf), bargs(U1, Un, U2, tiles_f, nf), bargs(U2, Un, Un, tiles_f, nf)};
     cudaGraphExec_t exec = nullptr;
-    if (last0 > 0 && (rc = get_batched_graph(prob, dev, 127, grid_f, a3, &exec)) != WT_OK) return rc;
+    if (last0 > 0 && (rc = get_batched_graph(prob, dev, kFwdTile, grid_f, a3, &exec)) != WT_OK) return rc;
     for (int64_t step = 0; step < last0; ++step) {
       if (step % K == 0) WT_CUDA(cudaMemcpyAsync(ckpt + (size_t)(step / K) * 3 * P, Un, plane_bytes, cudaMemcpyDeviceToDevice, st));
       WT_CUDA(cudaGraphLaunch(exec, st));
@@ -1411,6 +1425,7 @@ int weno_theta_adjoint(const wt_problem* prob, const wt_grid* grid, int32_t npro
         aa.goff = goff;
         aa.G = Gbuf;
         aa.partial = partial;
+        aa.rec = recs(k, s);
         WT_CUDA(strict ? launch_adj_stage_strict(aa, grid_r, adj_code, st) : launch_adj_stage_fast(aa, grid_r, adj_code, st));
         GatherArgs ga;
         memset(&ga, 0, sizeof ga);

@@ -232,7 +232,7 @@ struct AlphaWait {
 // written and then gathered by the last warp while the others go on).  Returns false if a
 // wait for the alphas timed out (the flag word then holds 2) or, at the first stage of a
 // step-blocked RK step, if some CTA has seen a failure (flag word 3): the step is not taken.
-template <class MATH, int FLUX, int STAGE, int T, int MODE, int IPT = 1>
+template <class MATH, int FLUX, int STAGE, int T, int MODE, int IPT = 1, bool REC = false>
 __device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long long js, const int Ts, const int off,
                                                 const long long own_lo, const long long own_hi,
                                                 double (&alpha)[FluxM<FLUX>::m], double& dt, double* sm,
@@ -479,6 +479,11 @@ __device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long
       if (aw.clear >= 0 && tid == 0) ctl->dt = dt;
     }
   }
+  // REC (the adjoint's recording forward pass): each reconstruction's branch flags, bit 0 restricted
+  // (Eq. (be_res)), bit 1 theta = 1 (Eq. (tau_we6)), kept in the reduction buffer until the
+  // records are written (phase E reuses it afterwards)
+  unsigned char* s_fl = reinterpret_cast<unsigned char*>(s_red);
+  static_assert(!REC || (2 * M * NI <= 4 * 32 * 8 && MODE == kStage), "flags fit the reduction buffer");
   // one reconstruction (stencil q) into s_F[dst], or into the queue
   auto reconstruct = [&](const double* q, const int dst) {
     if constexpr (MATH::kSplitWeno && MODE == kStepBlocked) {
@@ -503,7 +508,9 @@ __device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long
       double out;
       if (MATH::weno_begin(q, a.eps, a.alpha_R, out, w)) {
         s_F[dst] = out;
+        if constexpr (REC) s_fl[dst] = (unsigned char)(1 | (w.theta1 ? 2 : 0));
       } else {
+        if constexpr (REC) s_fl[dst] = (unsigned char)(w.theta1 ? 2 : 0);
         const int slot = atomicAdd(s_qn, 1);
         if (slot < QCAP) {
 #pragma unroll
@@ -516,6 +523,10 @@ __device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long
           s_F[dst] = MATH::weno_finish(w);
         }
       }
+    } else if constexpr (REC) {
+      bool r, t;
+      s_F[dst] = MATH::weno_flags(q, a.eps, a.alpha_R, r, t);
+      s_fl[dst] = (unsigned char)((r ? 1 : 0) | (t ? 2 : 0));
     } else {
       s_F[dst] = MATH::weno(q, a.eps, a.alpha_R);
     }
@@ -601,6 +612,27 @@ __device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long
       }
       __syncthreads();
     }
+  }
+
+  // REC: the records of the tile's interfaces (slot js + i for interface js - 1 + i; a tile
+  // shares its first interface with its left neighbour, which writes the same values)
+  if constexpr (REC) {
+    for (int i = tid; i < ni; i += NT) {
+      double* r = a.rec + (size_t)(js + i) * kAdjRec;
+      unsigned long long fl = 0ull;
+#pragma unroll
+      for (int side = 0; side < 2; ++side)
+#pragma unroll
+        for (int f = 0; f < 3; ++f)
+          fl |= (unsigned long long)s_fl[side * (M * NI) + f * NI + i] << (2 * (3 * side + f));
+      r[0] = s_rs[i];
+      r[1] = s_rs[NI + i];
+      r[2] = s_F[i] + s_F[3 * NI + i];
+      r[3] = s_F[NI + i] + s_F[4 * NI + i];
+      r[4] = s_F[2 * NI + i] + s_F[5 * NI + i];
+      r[5] = __longlong_as_double((long long)fl);
+    }
+    __syncthreads();  // the flags' buffer is the reduction buffer of phase E
   }
 
   // ---- D: interface fluxes h_{j+1/2} = R (F+ + F-)
@@ -733,7 +765,7 @@ __device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long
   return true;
 }
 
-template <class MATH, int FLUX, int STAGE, int T, int IPT = 1>
+template <class MATH, int FLUX, int STAGE, int T, int IPT = 1, bool REC = false>
 __device__ __forceinline__ bool stage1d_tile(const Stage1DArgs& a, const long long j0, const bool first_tile, double* sm,
                                              uint32_t& phase) {
   constexpr int M = FluxM<FLUX>::m;
@@ -804,8 +836,8 @@ __device__ __forceinline__ bool stage1d_tile(const Stage1DArgs& a, const long lo
     ctl->active = 1;
   }
 
-  stage1d_compute<MATH, FLUX, STAGE, T, kStage, IPT>(a, j0, Tc, off, j0, j0 + Tc, alpha, dt, sm,
-                                                     AlphaWait{0ull, 0, -1, 0, 0.0, 0.0, 0.0, 0.0});
+  stage1d_compute<MATH, FLUX, STAGE, T, kStage, IPT, REC>(a, j0, Tc, off, j0, j0 + Tc, alpha, dt, sm,
+                                                          AlphaWait{0ull, 0, -1, 0, 0.0, 0.0, 0.0, 0.0});
   if (STAGE != STAGE_RHS) {
     if (STAGE == STAGE_RK3 && first_tile && tid == 0) {
       ctl->t = ctl->t + dt;
@@ -829,7 +861,7 @@ __global__ void __launch_bounds__(Tile1D<T, FluxM<FLUX>::m>::NT) stage1d_kernel(
 
 // Batched stage: a persistent grid walks a table of (problem, tile) work items over many
 // independent problems, each with its own grid, boundary conditions, alphas and dt.
-template <class MATH, int FLUX, int STAGE, int T, int IPT>
+template <class MATH, int FLUX, int STAGE, int T, int IPT, bool REC = false>
 __global__ void __launch_bounds__(Tile1D<T, FluxM<FLUX>::m, 1, IPT>::NT) stage1d_batched_kernel(const BatchArgs b) {
   using TL = Tile1D<T, FluxM<FLUX>::m, 1, IPT>;
   extern __shared__ __align__(16) double sm[];
@@ -858,8 +890,9 @@ __global__ void __launch_bounds__(Tile1D<T, FluxM<FLUX>::m, 1, IPT>::NT) stage1d
     a.bc_lo = sg.bc_lo;
     a.bc_hi = sg.bc_hi;
     a.ctl = b.ctl + item.x;
+    a.rec = REC ? b.rec + (size_t)b.rec_off[item.x] * kAdjRec : nullptr;
     const long long j0 = (long long)item.y * T;
-    if (!stage1d_tile<MATH, FLUX, STAGE, T, IPT>(a, j0, j0 == 0, sm, phase)) return;
+    if (!stage1d_tile<MATH, FLUX, STAGE, T, IPT, REC>(a, j0, j0 == 0, sm, phase)) return;
     __syncthreads();
   }
 }
@@ -1351,11 +1384,23 @@ cudaError_t launch_alpha1d_policy(int flux, const double* u, long long n, long l
   return cudaGetLastError();
 }
 
-template <class MATH, int FLUX, int STAGE, int T, int IPT>
+template <class MATH, int FLUX, int STAGE, int T, int IPT, bool REC = false>
 cudaError_t launch_stage1d_batched_t(const BatchArgs& b, int grid, cudaStream_t st) {
   using TL = Tile1D<T, FluxM<FLUX>::m, 1, IPT>;
   static_assert(TL::bytes <= 48 * 1024, "tile exceeds the default dynamic shared memory limit");
-  return launch_pdl(stage1d_batched_kernel<MATH, FLUX, STAGE, T, IPT>, dim3(grid), dim3(TL::NT), TL::bytes, st, b);
+  return launch_pdl(stage1d_batched_kernel<MATH, FLUX, STAGE, T, IPT, REC>, dim3(grid), dim3(TL::NT), TL::bytes, st,
+                    b);
+}
+
+// the adjoint's recording forward stage: 1D Euler, 127-cell tiles, six items per thread
+template <class MATH>
+cudaError_t launch_stage1d_batched_record_policy(int stage, const BatchArgs& b, int grid, cudaStream_t st) {
+  switch (stage) {
+    case STAGE_RK1: return launch_stage1d_batched_t<MATH, WT_FLUX_EULER1D, STAGE_RK1, 127, 6, true>(b, grid, st);
+    case STAGE_RK2: return launch_stage1d_batched_t<MATH, WT_FLUX_EULER1D, STAGE_RK2, 127, 6, true>(b, grid, st);
+    case STAGE_RK3: return launch_stage1d_batched_t<MATH, WT_FLUX_EULER1D, STAGE_RK3, 127, 6, true>(b, grid, st);
+  }
+  return cudaErrorInvalidValue;
 }
 
 template <class MATH, int FLUX, int T, int IPT = 1>

@@ -156,6 +156,10 @@ cudaError_t launch_stage1d_batched_fast(int flux, int stage, int tile, const Bat
   return launch_stage1d_batched_policy<FastMath>(flux, stage, tile, b, grid, st);
 }
 
+cudaError_t launch_stage1d_batched_record_fast(int stage, const BatchArgs& b, int grid, cudaStream_t st) {
+  return launch_stage1d_batched_record_policy<FastMath>(stage, b, grid, st);
+}
+
 cudaError_t launch_alpha1d_batched_fast(int flux, const double* u, long long pitch, const BatchSeg* segs, int nprob,
                                         long long maxn, double gamma, double adv, Ctl* ctl, cudaStream_t st) {
   return launch_alpha1d_batched_policy<FastMath>(flux, u, pitch, segs, nprob, maxn, gamma, adv, ctl, st);

@@ -32,6 +32,10 @@ cudaError_t launch_stage1d_batched_strict(int flux, int stage, int tile, const B
   return launch_stage1d_batched_policy<StrictMath>(flux, stage, tile, b, grid, st);
 }
 
+cudaError_t launch_stage1d_batched_record_strict(int stage, const BatchArgs& b, int grid, cudaStream_t st) {
+  return launch_stage1d_batched_record_policy<StrictMath>(stage, b, grid, st);
+}
+
 cudaError_t launch_alpha1d_batched_strict(int flux, const double* u, long long pitch, const BatchSeg* segs, int nprob,
                                         long long maxn, double gamma, double adv, Ctl* ctl, cudaStream_t st) {
   return launch_alpha1d_batched_policy<StrictMath>(flux, u, pitch, segs, nprob, maxn, gamma, adv, ctl, st);

@@ -22,7 +22,17 @@ struct Stage1DArgs {
   double gamma, adv_speed, eps, alpha_R;
   int bc_lo, bc_hi;
   Ctl* ctl;
+  // the adjoint's recording forward pass only (else null): one record of kAdjRec doubles per
+  // interface, slot gi + 1 for interface gi = -1 .. n-1
+  double* rec;
 };
+
+// Record of one interface and stage for the adjoint's reverse pass: Roe's mean velocity and
+// enthalpy (from which the policy rebuilds the eigenvectors bit for bit), the characteristic
+// fluxes F_s = F+_s + F-_s of the three fields, and the branch flags of the six
+// reconstructions as the bit pattern of a double: bit 2 (3 side + s) set if restricted (Eq.
+// (be_res)), bit 2 (3 side + s) + 1 set if theta = 1 (Eq. (tau_we6)); side 0 = +, 1 = -.
+constexpr int kAdjRec = 6;
 
 // Arguments of the persistent kernel: the three stages of an RK step and the steps to take
 struct PersistArgs {
@@ -57,6 +67,8 @@ struct BatchArgs {
   const int2* tiles;       // work items: (problem, tile index); tile j0 = index * T
   int ntiles;
   double gamma, adv_speed, eps, alpha_R;
+  double* rec;             // recording forward pass of the adjoint only (else null): records
+  const long long* rec_off;  // [nprob] first interface slot of each problem in rec
 };
 
 // tile: a tile code, cells per tile + 1000 x (items per thread - 1): 31, 63, 127 (Euler; 63, 127
@@ -64,6 +76,9 @@ struct BatchArgs {
 // 2127, 3127 and 5127 (Euler) with three, four and six
 cudaError_t launch_stage1d_batched_strict(int flux, int stage, int tile, const BatchArgs& b, int grid, cudaStream_t st);
 cudaError_t launch_stage1d_batched_fast(int flux, int stage, int tile, const BatchArgs& b, int grid, cudaStream_t st);
+// the adjoint's recording forward stage (1D Euler, tile code 5127): also writes b.rec
+cudaError_t launch_stage1d_batched_record_strict(int stage, const BatchArgs& b, int grid, cudaStream_t st);
+cudaError_t launch_stage1d_batched_record_fast(int stage, const BatchArgs& b, int grid, cudaStream_t st);
 // resident CTAs per SM of the batched stage kernel (occupancy), 0 on error
 int stage1d_batched_occupancy_strict(int flux, int tile);
 int stage1d_batched_occupancy_fast(int flux, int tile);
@@ -125,6 +140,7 @@ struct AdjArgs {  // one reverse RK stage over a tile table
   const long long* goff;    // [nprob]: first interface slot of the problem in G (n + 1 slots)
   double* G;                // [slots][36]: per interface, 6 cells x (fbar[3], Ubar[3])
   double* partial;          // [ntiles][4]: d/d alpha_s (3) and d/d dt of the tile
+  const double* rec;        // [slots][kAdjRec] the forward stage's records (slots as G)
 };
 
 struct GatherArgs {  // per-cell gather of the interface contributions

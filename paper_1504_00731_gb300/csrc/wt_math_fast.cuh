@@ -89,6 +89,11 @@ struct FastMath {
     const double wa = sa * is, wb = sb * is;
     const double u = dot2(wa, ua, wb, ub);
     const double H = dot2(wa, Ha, wb, Hb);
+    roe_mean(u, H, gamma, L, rs);
+  }
+  // the (1/2-scaled) left eigenvectors and (u, H, c) from Roe's mean velocity and enthalpy,
+  // exactly as roe() forms them
+  __device__ __forceinline__ static void roe_mean(double u, double H, double gamma, double* L, double* rs) {
     const double gm1 = gamma - 1.0;
     const double c2 = gm1 * fma(-0.5 * u, u, H);
     const double ic = rsqrt(c2);
@@ -156,6 +161,10 @@ struct FastMath {
                                                      double& b) {
     a = fma(l[2], f[2], fma(l[1], f[1], l[0] * f[0]));
     b = fma(l[2], U[2], fma(l[1], U[1], l[0] * U[0]));
+  }
+  // the l.u half of project3_ab alone, with the same operations
+  __device__ __forceinline__ static double project3_b(const double* l, const double* U) {
+    return fma(l[2], U[2], fma(l[1], U[1], l[0] * U[0]));
   }
   __device__ __forceinline__ static void project1_ab(double f, double u, double& a, double& b) {
     a = 0.5 * f;

@@ -67,6 +67,10 @@ struct StrictMath {
                                              double gamma, double* L, double* rs) {
     double u = (sa * ua + sb * ub) / (sa + sb);
     double H = (sa * Ha + sb * Hb) / (sa + sb);
+    roe_mean(u, H, gamma, L, rs);
+  }
+  // the eigenvectors from Roe's mean velocity and enthalpy, exactly as roe() forms them
+  __device__ __forceinline__ static void roe_mean(double u, double H, double gamma, double* L, double* rs) {
     double c = sqrt((gamma - 1.0) * (H - 0.5 * u * u));
     double b1 = (gamma - 1.0) / (c * c);
     double b2 = 0.5 * u * u * b1;
@@ -112,6 +116,13 @@ struct StrictMath {
     b = b + l[1] * U[1];
     a = a + l[2] * f[2];
     b = b + l[2] * U[2];
+  }
+  // the l.u half of project3_ab alone, with the same operations
+  __device__ __forceinline__ static double project3_b(const double* l, const double* U) {
+    double b = l[0] * U[0];
+    b = b + l[1] * U[1];
+    b = b + l[2] * U[2];
+    return b;
   }
   __device__ __forceinline__ static void project1_ab(double f, double u, double& a, double& b) {
     a = f;
