@@ -20,25 +20,31 @@ struct FluxM {
 // per side of the reconstruction (two warps per SMSP where the tile fills one warp per SMSP).
 // IPT > 1 (stage and batched tiles): each thread carries IPT (interface, field) items, so the
 // tile has about a 1/IPT of the threads and each thread IPT times the work of every phase.
-template <int T, int M, int SPLIT = 1, int IPT = 1>
+// LATE (the stage and batched tiles, kStage): the eigenvector buffer, dead once phase C1 is
+// done, also holds the interface fluxes h of phase D and the window of u^n, which is copied in
+// after phase C1 (stages 2, 3) instead of with the stage input, so a tile needs about a sixth
+// less shared memory and one more tile fits on an SM.
+template <int T, int M, int SPLIT = 1, int IPT = 1, bool LATE = false>
 struct Tile1D {
   static_assert(IPT == 1 || SPLIT == 1, "thread pairs carry one item");
+  static_assert(!LATE || SPLIT == 1, "the late u^n window is for the stage tiles");
   static constexpr int W = (T + 9) & ~1;              // staged window: T + 6 cells + alignment slack, even
   static constexpr int NI = T + 1;
   static constexpr int NT = SPLIT * ((M * NI + 32 * IPT - 1) / (32 * IPT)) * 32;
   // shared-memory layout in doubles
   static constexpr int kBar = 0;
   static constexpr int kUin = 2;
-  static constexpr int kUn = kUin + M * W;
-  static constexpr int kF = kUn + M * W;
+  static constexpr int kF = kUin + (LATE ? 1 : 2) * M * W;
   static constexpr int kVel = kF + M * W;
   static constexpr int kH = kVel + W;
   static constexpr int kSr = kH + W;
   static constexpr int kL = kSr + W;
   static constexpr int kRs = kL + 9 * NI;
   static constexpr int kFs = kRs + 3 * NI;       // F+ [M][NI], then F- [M][NI]
-  static constexpr int kHf = kFs + 2 * M * NI;
-  static constexpr int kRed = kHf + M * NI;
+  static constexpr int kHf = LATE ? kL : kFs + 2 * M * NI;
+  static constexpr int kUn = LATE ? kL + M * NI : kUin + M * W;
+  static_assert(!LATE || (M * NI + M * W <= 9 * NI && (kUn % 2) == 0), "h and u^n fit the eigenvector buffer");
+  static constexpr int kRed = LATE ? kFs + 2 * M * NI : kHf + M * NI;
   static constexpr int kQn = kRed + 4 * 32;      // queue length (int)
   // queue of reconstructions still to be completed: one slot per thread, fewer if the tile
   // would pass 48 KB (the rest are completed in place).  A record holds the weights' inputs
@@ -236,12 +242,13 @@ template <class MATH, int FLUX, int STAGE, int T, int MODE, int IPT = 1, bool RE
 __device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long long js, const int Ts, const int off,
                                                 const long long own_lo, const long long own_hi,
                                                 double (&alpha)[FluxM<FLUX>::m], double& dt, double* sm,
-                                                const AlphaWait aw) {
+                                                const AlphaWait aw, uint32_t* phase = nullptr) {
   constexpr int M = FluxM<FLUX>::m;
   // step-blocked tiles split each reconstruction pair over two threads (see phase C1)
   constexpr int SPLIT = (MODE == kStepBlocked) ? 2 : 1;
   static_assert(IPT == 1 || MODE != kStepBlocked, "the step-blocked tiles carry one item per thread pair");
-  using TL = Tile1D<T, M, SPLIT, IPT>;
+  constexpr bool LATE = (MODE == kStage);
+  using TL = Tile1D<T, M, SPLIT, IPT, LATE>;
   constexpr int W = TL::W, NI = TL::NI, NT = TL::NT;
   static_assert(NT * IPT >= SPLIT * M * NI, "IPT (interface, field) items per thread (one per thread pair with SPLIT = 2)");
   double* s_uin = sm + TL::kUin;
@@ -579,6 +586,19 @@ __device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long
     }
   }
   __syncthreads();
+  // LATE: phase C1 no longer reads the eigenvectors, so the window of u^n (stages 2, 3) is copied
+  // into their buffer now; it lands while the queued weights and phase D run
+  [[maybe_unused]] uint64_t* s_bar = reinterpret_cast<uint64_t*>(sm + TL::kBar);
+  if constexpr (LATE && kNeedUn) {
+    if (tid == 0) {
+      const uint32_t late_bytes = (uint32_t)(((off + Tc + 2 * G + 1) & ~1) * 8);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // after the generic reads of the buffer
+      mbar_arrive_expect_tx(s_bar, late_bytes * M);
+      const long long s0 = js & ~1LL;
+#pragma unroll
+      for (int c = 0; c < M; ++c) bulk_g2s(s_un + c * W, a.un + c * a.pitch + s0, late_bytes, s_bar);
+    }
+  }
   if constexpr (MATH::kSplitWeno) {
     const int nq = min(*s_qn, QCAP);  // the same for every thread of the block
     if (nq > 0 && MODE == kStepBlocked) {
@@ -650,6 +670,16 @@ __device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long
     hsrc = s_h;
   }
 
+  // LATE: the window of u^n has landed before phase E reads it (bounded wait)
+  if constexpr (LATE && kNeedUn) {
+    const bool ok = mbar_wait_bounded(s_bar, *phase);
+    if (__syncthreads_or(ok ? 0 : 1)) {
+      if (tid == 0) flag_error(ctl, WT_ERR_TIMEOUT);
+      mbar_wait_bounded(s_bar, *phase);
+      return false;
+    }
+    *phase ^= 1u;
+  }
   // ---- E: flux difference, RK combine, ghost images, wave speeds.  Step-blocked: one
   // (cell, component) per thread, and no wave speeds (phase B of the next stage takes them).
   if (MODE == kStepBlocked && STAGE != STAGE_RHS) {
@@ -769,11 +799,10 @@ template <class MATH, int FLUX, int STAGE, int T, int IPT = 1, bool REC = false>
 __device__ __forceinline__ bool stage1d_tile(const Stage1DArgs& a, const long long j0, const bool first_tile, double* sm,
                                              uint32_t& phase) {
   constexpr int M = FluxM<FLUX>::m;
-  using TL = Tile1D<T, M, 1, IPT>;
+  using TL = Tile1D<T, M, 1, IPT, true>;
   constexpr int W = TL::W;
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + TL::kBar);
   double* s_uin = sm + TL::kUin;
-  double* s_un = sm + TL::kUn;
   int* s_run = reinterpret_cast<int*>(sm + TL::kQn) + 1;
   const int tid = threadIdx.x;
   Ctl* ctl = a.ctl;
@@ -788,15 +817,12 @@ __device__ __forceinline__ bool stage1d_tile(const Stage1DArgs& a, const long lo
   const int cells = Tc + 2 * G;
   const int len = (off + cells + 1) & ~1;
   constexpr bool kNeedUn = (STAGE == STAGE_RK2 || STAGE == STAGE_RK3);
+  // (u^n of stages 2 and 3 is copied later, into the eigenvector buffer: Tile1D LATE)
   if (tid == 0) {
     const uint32_t bytes = (uint32_t)len * 8u;
-    mbar_arrive_expect_tx(bar, bytes * (kNeedUn ? 2 * M : M));
+    mbar_arrive_expect_tx(bar, bytes * M);
 #pragma unroll
     for (int c = 0; c < M; ++c) bulk_g2s(s_uin + c * W, a.uin + c * a.pitch + s0, bytes, bar);
-    if (kNeedUn) {
-#pragma unroll
-      for (int c = 0; c < M; ++c) bulk_g2s(s_un + c * W, a.un + c * a.pitch + s0, bytes, bar);
-    }
   }
 
   // ---- step control: is this step active (decided by thread 0 for the whole block), its dt
@@ -836,8 +862,9 @@ __device__ __forceinline__ bool stage1d_tile(const Stage1DArgs& a, const long lo
     ctl->active = 1;
   }
 
-  stage1d_compute<MATH, FLUX, STAGE, T, kStage, IPT, REC>(a, j0, Tc, off, j0, j0 + Tc, alpha, dt, sm,
-                                                          AlphaWait{0ull, 0, -1, 0, 0.0, 0.0, 0.0, 0.0});
+  if (!stage1d_compute<MATH, FLUX, STAGE, T, kStage, IPT, REC>(a, j0, Tc, off, j0, j0 + Tc, alpha, dt, sm,
+                                                              AlphaWait{0ull, 0, -1, 0, 0.0, 0.0, 0.0, 0.0}, &phase))
+    return false;
   if (STAGE != STAGE_RHS) {
     if (STAGE == STAGE_RK3 && first_tile && tid == 0) {
       ctl->t = ctl->t + dt;
@@ -848,8 +875,8 @@ __device__ __forceinline__ bool stage1d_tile(const Stage1DArgs& a, const long lo
 }
 
 template <class MATH, int FLUX, int STAGE, int T>
-__global__ void __launch_bounds__(Tile1D<T, FluxM<FLUX>::m>::NT) stage1d_kernel(const Stage1DArgs a) {
-  using TL = Tile1D<T, FluxM<FLUX>::m>;
+__global__ void __launch_bounds__(Tile1D<T, FluxM<FLUX>::m, 1, 1, true>::NT) stage1d_kernel(const Stage1DArgs a) {
+  using TL = Tile1D<T, FluxM<FLUX>::m, 1, 1, true>;
   extern __shared__ __align__(16) double sm[];
   pdl_launch_dependents();
   if (threadIdx.x == 0) mbar_init(reinterpret_cast<uint64_t*>(sm + TL::kBar), 1);
@@ -862,8 +889,8 @@ __global__ void __launch_bounds__(Tile1D<T, FluxM<FLUX>::m>::NT) stage1d_kernel(
 // Batched stage: a persistent grid walks a table of (problem, tile) work items over many
 // independent problems, each with its own grid, boundary conditions, alphas and dt.
 template <class MATH, int FLUX, int STAGE, int T, int IPT, bool REC = false>
-__global__ void __launch_bounds__(Tile1D<T, FluxM<FLUX>::m, 1, IPT>::NT) stage1d_batched_kernel(const BatchArgs b) {
-  using TL = Tile1D<T, FluxM<FLUX>::m, 1, IPT>;
+__global__ void __launch_bounds__(Tile1D<T, FluxM<FLUX>::m, 1, IPT, true>::NT) stage1d_batched_kernel(const BatchArgs b) {
+  using TL = Tile1D<T, FluxM<FLUX>::m, 1, IPT, true>;
   extern __shared__ __align__(16) double sm[];
   pdl_launch_dependents();
   if (threadIdx.x == 0) mbar_init(reinterpret_cast<uint64_t*>(sm + TL::kBar), 1);
@@ -1223,7 +1250,7 @@ cudaError_t launch_pdl(K kern, dim3 grid, dim3 block, size_t smem, cudaStream_t 
 }
 template <class MATH, int FLUX, int STAGE, int T>
 cudaError_t launch_stage1d_t(const Stage1DArgs& a, cudaStream_t st) {
-  using TL = Tile1D<T, FluxM<FLUX>::m>;
+  using TL = Tile1D<T, FluxM<FLUX>::m, 1, 1, true>;
   static_assert(TL::bytes <= 48 * 1024, "tile exceeds the default dynamic shared memory limit");
   auto kern = stage1d_kernel<MATH, FLUX, STAGE, T>;
   const unsigned grid = (unsigned)((a.n + T - 1) / T);
@@ -1386,7 +1413,7 @@ cudaError_t launch_alpha1d_policy(int flux, const double* u, long long n, long l
 
 template <class MATH, int FLUX, int STAGE, int T, int IPT, bool REC = false>
 cudaError_t launch_stage1d_batched_t(const BatchArgs& b, int grid, cudaStream_t st) {
-  using TL = Tile1D<T, FluxM<FLUX>::m, 1, IPT>;
+  using TL = Tile1D<T, FluxM<FLUX>::m, 1, IPT, true>;
   static_assert(TL::bytes <= 48 * 1024, "tile exceeds the default dynamic shared memory limit");
   return launch_pdl(stage1d_batched_kernel<MATH, FLUX, STAGE, T, IPT, REC>, dim3(grid), dim3(TL::NT), TL::bytes, st,
                     b);
@@ -1438,7 +1465,7 @@ cudaError_t launch_stage1d_batched_policy(int flux, int stage, int tile, const B
 
 template <class MATH, int FLUX, int T, int IPT = 1>
 int batched_occupancy_t() {
-  using TL = Tile1D<T, FluxM<FLUX>::m, 1, IPT>;
+  using TL = Tile1D<T, FluxM<FLUX>::m, 1, IPT, true>;
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, stage1d_batched_kernel<MATH, FLUX, STAGE_RK2, T, IPT>,
                                                     TL::NT, TL::bytes) != cudaSuccess)
