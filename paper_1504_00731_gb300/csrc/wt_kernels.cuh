@@ -24,7 +24,10 @@ struct FluxM {
 // done, also holds the interface fluxes h of phase D and the window of u^n, which is copied in
 // after phase C1 (stages 2, 3) instead of with the stage input, so a tile needs about a sixth
 // less shared memory and one more tile fits on an SM.
-template <int T, int M, int SPLIT = 1, int IPT = 1, bool LATE = false>
+// DP (the fast policy's 1D Euler tiles, MATH::kDiffProj): the differences of f and u between
+// neighbouring cells, taken once per stage after phase C0; those of f go to the planes of the
+// per-cell Roe inputs (dead once phase C0 is done), those of u to planes of their own.
+template <int T, int M, int SPLIT = 1, int IPT = 1, bool LATE = false, bool DP = false>
 struct Tile1D {
   static_assert(IPT == 1 || SPLIT == 1, "thread pairs carry one item");
   static_assert(!LATE || SPLIT == 1, "the late u^n window is for the stage tiles");
@@ -44,7 +47,10 @@ struct Tile1D {
   static constexpr int kHf = LATE ? kL : kFs + 2 * M * NI;
   static constexpr int kUn = LATE ? kL + M * NI : kUin + M * W;
   static_assert(!LATE || (M * NI + M * W <= 9 * NI && (kUn % 2) == 0), "h and u^n fit the eigenvector buffer");
-  static constexpr int kRed = LATE ? kFs + 2 * M * NI : kHf + M * NI;
+  static constexpr int kDf = kVel;                // DP: [M][W] f_{k+1} - f_k
+  static constexpr int kDu = LATE ? kFs + 2 * M * NI : kHf + M * NI;  // DP: [M][W] u_{k+1} - u_k
+  static_assert(!DP || M == 3, "differences first: 1D Euler tiles");
+  static constexpr int kRed = kDu + (DP ? M * W : 0);
   static constexpr int kQn = kRed + 4 * 32;      // queue length (int)
   // queue of reconstructions still to be completed: one slot per thread, fewer if the tile
   // would pass 48 KB (the rest are completed in place).  A record holds the weights' inputs
@@ -57,6 +63,10 @@ struct Tile1D {
   static constexpr int kTotal = kQi + QCAP / 2;
   static constexpr size_t bytes = sizeof(double) * kTotal;
 };
+
+// the tile of a policy and flux: differences first where the policy takes them (1D Euler)
+template <class MATH, int FLUX, int T, int SPLIT = 1, int IPT = 1, bool LATE = false>
+using TileOf = Tile1D<T, FluxM<FLUX>::m, SPLIT, IPT, LATE, MATH::kDiffProj && FLUX == WT_FLUX_EULER1D>;
 
 // ---------------------------------------------------------------------------------------
 // Boundary fill: copies the caller's state into the padded layout and writes the ghost
@@ -248,8 +258,9 @@ __device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long
   constexpr int SPLIT = (MODE == kStepBlocked) ? 2 : 1;
   static_assert(IPT == 1 || MODE != kStepBlocked, "the step-blocked tiles carry one item per thread pair");
   constexpr bool LATE = (MODE == kStage);
-  using TL = Tile1D<T, M, SPLIT, IPT, LATE>;
+  using TL = TileOf<MATH, FLUX, T, SPLIT, IPT, LATE>;
   constexpr int W = TL::W, NI = TL::NI, NT = TL::NT;
+  constexpr bool DP = MATH::kDiffProj && FLUX == WT_FLUX_EULER1D;  // differences first (phase C1)
   static_assert(NT * IPT >= SPLIT * M * NI, "IPT (interface, field) items per thread (one per thread pair with SPLIT = 2)");
   double* s_uin = sm + TL::kUin;
   double* s_un = sm + TL::kUn;
@@ -405,6 +416,23 @@ __device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long
     }
     c0_barrier();
   }
+  // DP: the differences of f and u between neighbouring window cells (f's over the per-cell
+  // Roe inputs, read for the last time in phase C0), by the threads of phase C0
+  double* s_df = sm + TL::kDf;
+  double* s_du = sm + TL::kDu;
+  if constexpr (DP) {
+    if (!(sw_free && (tid >> 5) == kSW)) {
+      const int np = sw_free ? NT - 32 : NT;
+      for (int k = tid; k < cells - 1; k += np) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          s_df[c * W + k] = s_f[c * W + k + 1] - s_f[c * W + k];
+          s_du[c * W + k] = s_uin[c * W + off + k + 1] - s_uin[c * W + off + k];
+        }
+      }
+    }
+    c0_barrier();
+  }
 
   // ---- C1: per (interface, field) reconstruction on both sides.  The projections onto the
   // characteristic field split into the alpha-free products (l.f, l.u), taken first, and the
@@ -425,7 +453,61 @@ __device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long
   // pa, pb: (l.f, l.u) of the stencil cells i .. i + 5 (window index), in the order of the
   // side's stencil with SPLIT = 2 (the - side reads the cells mirrored, Eq. (flux_split_lf))
   double pa[6], pb[6];
-  if constexpr (SPLIT == 2) {
+  // DP: (da_k, db_k) the products of the stencil's cell differences, (a2, b2) and (a3, b3) those
+  // of its two centre cells (MATH::side_diffs); with SPLIT = 2 the + thread takes the centre
+  // cell 2 and differences 0, 1, the - thread cell 3 and differences 4, 3, and the pair swaps them
+  double da[5], db[5], a2 = 0.0, b2 = 0.0, a3 = 0.0, b3 = 0.0;
+  auto proj_cell = [&](const double* l, const int k, double& x, double& y) {
+    double f[3] = {s_f[k], s_f[W + k], s_f[2 * W + k]};
+    double U[3] = {s_uin[off + k], s_uin[W + off + k], s_uin[2 * W + off + k]};
+    MATH::project3_ab(l, f, U, x, y);
+  };
+  auto proj_diff = [&](const double* l, const int k, double& x, double& y) {
+    double f[3] = {s_df[k], s_df[W + k], s_df[2 * W + k]};
+    double U[3] = {s_du[k], s_du[W + k], s_du[2 * W + k]};
+    MATH::project3_ab(l, f, U, x, y);
+  };
+  if constexpr (DP && SPLIT == 2) {
+    double o[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    if (has_item) {
+      double l[3] = {s_L[(3 * s) * NI + i], s_L[(3 * s + 1) * NI + i], s_L[(3 * s + 2) * NI + i]};
+      proj_cell(l, i + 2 + side2, o[0], o[1]);
+      proj_diff(l, side2 ? i + 4 : i, o[2], o[3]);
+      proj_diff(l, side2 ? i + 3 : i + 1, o[4], o[5]);
+    }
+    if ((tid >> 5) * 32 < SPLIT * M * ni) {
+      double p[6];
+#pragma unroll
+      for (int r = 0; r < 6; ++r) p[r] = __shfl_xor_sync(0xffffffffu, o[r], 1);
+      const bool mi = side2 != 0;
+      a2 = mi ? p[0] : o[0];
+      b2 = mi ? p[1] : o[1];
+      a3 = mi ? o[0] : p[0];
+      b3 = mi ? o[1] : p[1];
+      da[0] = mi ? p[2] : o[2];
+      db[0] = mi ? p[3] : o[3];
+      da[1] = mi ? p[4] : o[4];
+      db[1] = mi ? p[5] : o[5];
+      da[4] = mi ? o[2] : p[2];
+      db[4] = mi ? o[3] : p[3];
+      da[3] = mi ? o[4] : p[4];
+      db[3] = mi ? o[5] : p[5];
+      da[2] = a3 - a2;
+      db[2] = b3 - b2;
+    }
+  } else if constexpr (DP) {
+    if (has_item && IPT == 1) {
+      double l[3] = {s_L[(3 * s) * NI + i], s_L[(3 * s + 1) * NI + i], s_L[(3 * s + 2) * NI + i]};
+      proj_cell(l, i + 2, a2, b2);
+      proj_cell(l, i + 3, a3, b3);
+      proj_diff(l, i, da[0], db[0]);
+      proj_diff(l, i + 1, da[1], db[1]);
+      proj_diff(l, i + 3, da[3], db[3]);
+      proj_diff(l, i + 4, da[4], db[4]);
+      da[2] = a3 - a2;
+      db[2] = b3 - b2;
+    }
+  } else if constexpr (SPLIT == 2) {
     double oa[3] = {0.0, 0.0, 0.0}, ob[3] = {0.0, 0.0, 0.0};
     if (has_item) {
       if (FLUX == WT_FLUX_EULER1D) {
@@ -538,7 +620,79 @@ __device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long
       s_F[dst] = MATH::weno(q, a.eps, a.alpha_R);
     }
   };
-  if constexpr (IPT > 1) {
+  if constexpr (DP) {
+    // differences first: the reconstructions from their stencils' differences and q_2
+    auto reconstruct_d = [&](const double* d, const double q2, const int dst) {
+      double out;
+      if constexpr (MODE == kStepBlocked) {
+        double rec[TL::REC];
+        if (MATH::weno_front_d(d, q2, a.eps, a.alpha_R, out, rec)) {
+          s_F[dst] = out;
+        } else {
+          const int slot = atomicAdd(s_qn, 1);
+          if (slot < QCAP) {
+#pragma unroll
+            for (int r = 0; r < TL::REC; ++r) s_q[r * QCAP + slot] = rec[r];
+            s_qi[slot] = dst;
+          } else {
+            s_F[dst] = MATH::weno_d(d, q2, a.eps, a.alpha_R);
+          }
+        }
+      } else {
+        typename MATH::WenoPart w;
+        if (MATH::weno_begin_d(d, q2, a.eps, a.alpha_R, out, w)) {
+          s_F[dst] = out;
+          if constexpr (REC) s_fl[dst] = (unsigned char)(1 | (w.theta1 ? 2 : 0));
+        } else {
+          if constexpr (REC) s_fl[dst] = (unsigned char)(w.theta1 ? 2 : 0);
+          const int slot = atomicAdd(s_qn, 1);
+          if (slot < QCAP) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) s_q[k * QCAP + slot] = w.e[k];
+            s_q[4 * QCAP + slot] = w.tau;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) s_q[(5 + k) * QCAP + slot] = w.fh[k];
+            s_qi[slot] = dst | (w.theta1 ? (1 << 30) : 0);
+          } else {
+            s_F[dst] = MATH::weno_finish(w);
+          }
+        }
+      }
+    };
+    if constexpr (IPT > 1) {
+      for (int it2 = tid; it2 < M * ni; it2 += NT) {
+        const int s2 = it2 / ni, i2 = it2 - s2 * ni;
+        double l[3] = {s_L[(3 * s2) * NI + i2], s_L[(3 * s2 + 1) * NI + i2], s_L[(3 * s2 + 2) * NI + i2]};
+        double ea[5], eb[5], c2a, c2b, c3a, c3b;
+        proj_cell(l, i2 + 2, c2a, c2b);
+        proj_cell(l, i2 + 3, c3a, c3b);
+        proj_diff(l, i2, ea[0], eb[0]);
+        proj_diff(l, i2 + 1, ea[1], eb[1]);
+        proj_diff(l, i2 + 3, ea[3], eb[3]);
+        proj_diff(l, i2 + 4, ea[4], eb[4]);
+        ea[2] = c3a - c2a;
+        eb[2] = c3b - c2b;
+        const double al = (s2 == 0) ? alpha[0] : ((s2 == 1) ? alpha[1] : alpha[M - 1]);
+        double d[5], q2;
+        MATH::side_diffs(ea, eb, c2a, c2b, c3a, c3b, al, false, d, q2);
+        reconstruct_d(d, q2, s2 * NI + i2);
+        MATH::side_diffs(ea, eb, c2a, c2b, c3a, c3b, al, true, d, q2);
+        reconstruct_d(d, q2, M * NI + s2 * NI + i2);
+      }
+    } else if (has_item) {
+      const double al = (s == 0) ? alpha[0] : ((s == 1) ? alpha[1] : alpha[M - 1]);
+      double d[5], q2;
+      if constexpr (SPLIT == 2) {
+        MATH::side_diffs(da, db, a2, b2, a3, b3, al, side2 != 0, d, q2);
+        reconstruct_d(d, q2, side2 * (M * NI) + s * NI + i);
+      } else {
+        MATH::side_diffs(da, db, a2, b2, a3, b3, al, false, d, q2);
+        reconstruct_d(d, q2, s * NI + i);
+        MATH::side_diffs(da, db, a2, b2, a3, b3, al, true, d, q2);
+        reconstruct_d(d, q2, M * NI + s * NI + i);
+      }
+    }
+  } else if constexpr (IPT > 1) {
     // several items per thread: projection and both reconstructions of each item in turn, with
     // the operations of the one-item path
     for (int it2 = tid; it2 < M * ni; it2 += NT) {
@@ -799,7 +953,7 @@ template <class MATH, int FLUX, int STAGE, int T, int IPT = 1, bool REC = false>
 __device__ __forceinline__ bool stage1d_tile(const Stage1DArgs& a, const long long j0, const bool first_tile, double* sm,
                                              uint32_t& phase) {
   constexpr int M = FluxM<FLUX>::m;
-  using TL = Tile1D<T, M, 1, IPT, true>;
+  using TL = TileOf<MATH, FLUX, T, 1, IPT, true>;
   constexpr int W = TL::W;
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + TL::kBar);
   double* s_uin = sm + TL::kUin;
@@ -876,7 +1030,7 @@ __device__ __forceinline__ bool stage1d_tile(const Stage1DArgs& a, const long lo
 
 template <class MATH, int FLUX, int STAGE, int T>
 __global__ void __launch_bounds__(Tile1D<T, FluxM<FLUX>::m, 1, 1, true>::NT) stage1d_kernel(const Stage1DArgs a) {
-  using TL = Tile1D<T, FluxM<FLUX>::m, 1, 1, true>;
+  using TL = TileOf<MATH, FLUX, T, 1, 1, true>;
   extern __shared__ __align__(16) double sm[];
   pdl_launch_dependents();
   if (threadIdx.x == 0) mbar_init(reinterpret_cast<uint64_t*>(sm + TL::kBar), 1);
@@ -890,7 +1044,7 @@ __global__ void __launch_bounds__(Tile1D<T, FluxM<FLUX>::m, 1, 1, true>::NT) sta
 // independent problems, each with its own grid, boundary conditions, alphas and dt.
 template <class MATH, int FLUX, int STAGE, int T, int IPT, bool REC = false>
 __global__ void __launch_bounds__(Tile1D<T, FluxM<FLUX>::m, 1, IPT, true>::NT) stage1d_batched_kernel(const BatchArgs b) {
-  using TL = Tile1D<T, FluxM<FLUX>::m, 1, IPT, true>;
+  using TL = TileOf<MATH, FLUX, T, 1, IPT, true>;
   extern __shared__ __align__(16) double sm[];
   pdl_launch_dependents();
   if (threadIdx.x == 0) mbar_init(reinterpret_cast<uint64_t*>(sm + TL::kBar), 1);
@@ -952,7 +1106,7 @@ __device__ __forceinline__ void load_halos(const double* uin, long long pitch, l
 template <class MATH, int FLUX, int T>
 __global__ void __launch_bounds__(Tile1D<T, FluxM<FLUX>::m>::NT) persist1d_kernel(const PersistArgs p) {
   constexpr int M = FluxM<FLUX>::m;
-  using TL = Tile1D<T, M>;
+  using TL = TileOf<MATH, FLUX, T>;
   constexpr int W = TL::W, NT = TL::NT;
   extern __shared__ __align__(16) double sm[];
   double* s_uin = sm + TL::kUin;
@@ -1137,7 +1291,7 @@ __global__ void __launch_bounds__(Tile1D<T + 4 * G, FluxM<FLUX>::m, 2>::NT, 1) s
   constexpr int M = FluxM<FLUX>::m;
   constexpr int E0 = 3 * G;   // halo cells per side at the start of a step
   constexpr int TB = T + 4 * G;  // cells computed in stage 1: T + 2 * (E0 - G)
-  using TL = Tile1D<TB, M, 2>;
+  using TL = TileOf<MATH, FLUX, TB, 2>;
   constexpr int W = TL::W;
   static_assert(W >= T + 2 * E0, "window of a step");
   extern __shared__ __align__(16) double sm[];
@@ -1250,7 +1404,7 @@ cudaError_t launch_pdl(K kern, dim3 grid, dim3 block, size_t smem, cudaStream_t 
 }
 template <class MATH, int FLUX, int STAGE, int T>
 cudaError_t launch_stage1d_t(const Stage1DArgs& a, cudaStream_t st) {
-  using TL = Tile1D<T, FluxM<FLUX>::m, 1, 1, true>;
+  using TL = TileOf<MATH, FLUX, T, 1, 1, true>;
   static_assert(TL::bytes <= 48 * 1024, "tile exceeds the default dynamic shared memory limit");
   auto kern = stage1d_kernel<MATH, FLUX, STAGE, T>;
   const unsigned grid = (unsigned)((a.n + T - 1) / T);
@@ -1260,7 +1414,7 @@ cudaError_t launch_stage1d_t(const Stage1DArgs& a, cudaStream_t st) {
 // Cooperative launch of the persistent kernel (grid = number of tiles, all co-resident)
 template <class MATH, int FLUX, int T>
 cudaError_t launch_persist1d_t(const PersistArgs& p, int grid, cudaStream_t st) {
-  using TL = Tile1D<T, FluxM<FLUX>::m>;
+  using TL = TileOf<MATH, FLUX, T>;
   static_assert(TL::bytes <= 48 * 1024, "tile exceeds the default dynamic shared memory limit");
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)grid);
@@ -1278,7 +1432,7 @@ cudaError_t launch_persist1d_t(const PersistArgs& p, int grid, cudaStream_t st) 
 // CTAs of the persistent kernel that fit on the device at once (0: no cooperative launch)
 template <class MATH, int FLUX, int T>
 int persist1d_capacity_t() {
-  using TL = Tile1D<T, FluxM<FLUX>::m>;
+  using TL = TileOf<MATH, FLUX, T>;
   int dev = 0, sms = 0, coop = 0, per = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return 0;
@@ -1292,7 +1446,7 @@ int persist1d_capacity_t() {
 // Cooperative launch of the step-blocked kernel (grid = number of tiles of T cells)
 template <class MATH, int FLUX, int T>
 cudaError_t launch_stepblock1d_t(const PersistArgs& p, int grid, cudaStream_t st) {
-  using TL = Tile1D<T + 4 * G, FluxM<FLUX>::m, 2>;
+  using TL = TileOf<MATH, FLUX, T + 4 * G, 2>;
   static_assert(TL::bytes <= 48 * 1024, "tile exceeds the default dynamic shared memory limit");
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)grid);
@@ -1309,7 +1463,7 @@ cudaError_t launch_stepblock1d_t(const PersistArgs& p, int grid, cudaStream_t st
 
 template <class MATH, int FLUX, int T>
 int stepblock1d_capacity_t() {
-  using TL = Tile1D<T + 4 * G, FluxM<FLUX>::m, 2>;
+  using TL = TileOf<MATH, FLUX, T + 4 * G, 2>;
   int dev = 0, sms = 0, coop = 0, per = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return 0;
@@ -1413,7 +1567,7 @@ cudaError_t launch_alpha1d_policy(int flux, const double* u, long long n, long l
 
 template <class MATH, int FLUX, int STAGE, int T, int IPT, bool REC = false>
 cudaError_t launch_stage1d_batched_t(const BatchArgs& b, int grid, cudaStream_t st) {
-  using TL = Tile1D<T, FluxM<FLUX>::m, 1, IPT, true>;
+  using TL = TileOf<MATH, FLUX, T, 1, IPT, true>;
   static_assert(TL::bytes <= 48 * 1024, "tile exceeds the default dynamic shared memory limit");
   return launch_pdl(stage1d_batched_kernel<MATH, FLUX, STAGE, T, IPT, REC>, dim3(grid), dim3(TL::NT), TL::bytes, st,
                     b);
@@ -1465,7 +1619,7 @@ cudaError_t launch_stage1d_batched_policy(int flux, int stage, int tile, const B
 
 template <class MATH, int FLUX, int T, int IPT = 1>
 int batched_occupancy_t() {
-  using TL = Tile1D<T, FluxM<FLUX>::m, 1, IPT, true>;
+  using TL = TileOf<MATH, FLUX, T, 1, IPT, true>;
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, stage1d_batched_kernel<MATH, FLUX, STAGE_RK2, T, IPT>,
                                                     TL::NT, TL::bytes) != cudaSuccess)

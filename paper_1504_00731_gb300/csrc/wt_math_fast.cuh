@@ -174,6 +174,24 @@ struct FastMath {
     vp = fma(alpha, b, a);
     vm = fma(-alpha, b, a);
   }
+  // Differences first (kDiffProj): with the products (da_k, db_k) = (l.(f_{k+1} - f_k),
+  // l.(u_{k+1} - u_k)) of the cell differences of an interface's stencil cells 0..5 (the middle
+  // one, k = 2, taken as the difference of the two centre cells' products (a2, b2), (a3, b3)),
+  // the + side's stencil differences are d_k = da_k + alpha db_k and its q_2 = a2 + alpha b2;
+  // the - side reads v- = a - alpha b mirrored, so d_k = alpha db_{4-k} - da_{4-k} and
+  // q_2 = a3 - alpha b3.  Branch-free in `minus`, which may differ between adjacent lanes.
+  static constexpr bool kDiffProj = true;
+  __device__ __forceinline__ static void side_diffs(const double* da, const double* db, double a2, double b2,
+                                                    double a3, double b3, double alpha, bool minus, double* d,
+                                                    double& q2) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      const double x = minus ? da[4 - k] : da[k];
+      const double y = minus ? db[4 - k] : db[k];
+      d[k] = fma(alpha, y, minus ? -x : x);
+    }
+    q2 = fma(minus ? -alpha : alpha, minus ? b3 : b2, minus ? a3 : a2);
+  }
   // one side of project_v: v+ (minus false) or v- (minus true), the same value
   __device__ __forceinline__ static double project_side(double a, double b, double alpha, bool minus) {
     return fma(minus ? -alpha : alpha, b, a);
@@ -268,8 +286,18 @@ struct FastMath {
 
   __device__ __forceinline__ static bool weno_begin(const double* q, double eps, double alpha_R, double& out,
                                                     WenoPart& w) {
-    constexpr double C1312 = 13.0 / 12.0, C1348 = 13.0 / 48.0;
     const double d0 = q[1] - q[0], d1 = q[2] - q[1], d2 = q[3] - q[2], d3 = q[4] - q[3], d4 = q[5] - q[4];
+    return weno_core<false>(d0, d1, d2, d3, d4, q[2], q[3], eps, alpha_R, out, w);
+  }
+  // the same from the stencil's differences d_k = q_{k+1} - q_k and q_2 (q_3 taken as q_2 + d_2)
+  __device__ __forceinline__ static bool weno_begin_d(const double* d, double q2, double eps, double alpha_R,
+                                                      double& out, WenoPart& w) {
+    return weno_core<true>(d[0], d[1], d[2], d[3], d[4], q2, 0.0, eps, alpha_R, out, w);
+  }
+  template <bool Q3D>
+  __device__ __forceinline__ static bool weno_core(double d0, double d1, double d2, double d3, double d4, double q2,
+                                                   double q3, double eps, double alpha_R, double& out, WenoPart& w) {
+    constexpr double C1312 = 13.0 / 12.0, C1348 = 13.0 / 48.0;
     const double s0 = d1 - d0, s1 = d2 - d1, s2 = d3 - d2, s3 = d4 - d3;
     // the large-stencil terms of Eqs. (tau_5), (tau_6)
     const double t5b = s2 - s1;                // -q1 + 3 q2 - 3 q3 + q4
@@ -280,7 +308,7 @@ struct FastMath {
     const int scr = screen(s0, s1, s2, s3, d1, d2, d3, t5a, t5b, t6a, t6b, eps, alpha_R);
     if (scr != 0) {
       w.theta1 = scr == 1;
-      out = linear_theta(d0, d1, d2, d3, d4, q[2], w.theta1);
+      out = linear_theta(d0, d1, d2, d3, d4, q2, w.theta1);
       return true;
     }
     // Eqs. (be0_cen)-(be3_cen)
@@ -302,14 +330,14 @@ struct FastMath {
     const double bmax = nmax(nmax(b0, b1), nmax(b2, b3));
     const double bmin = nmin(nmin(b0, b1), nmin(b2, b3));
     if (!(bits(fma(alpha_R, bmin, alpha_R * eps)) < bits(bmax))) {
-      out = linear_theta(d0, d1, d2, d3, d4, q[2], w.theta1);
+      out = linear_theta(d0, d1, d2, d3, d4, q2, w.theta1);
       return true;
     }
     // Eqs. (fh0)-(fh3) in difference form
-    w.fh[0] = fma(5.0 / 6.0, d1, fma(-1.0 / 3.0, d0, q[2]));
-    w.fh[1] = fma(1.0 / 6.0, d1, fma(1.0 / 3.0, d2, q[2]));
-    w.fh[2] = fma(2.0 / 3.0, d2, fma(-1.0 / 6.0, d3, q[2]));
-    w.fh[3] = fma(1.0 / 3.0, d4, fma(-5.0 / 6.0, d3, q[3]));
+    w.fh[0] = fma(5.0 / 6.0, d1, fma(-1.0 / 3.0, d0, q2));
+    w.fh[1] = fma(1.0 / 6.0, d1, fma(1.0 / 3.0, d2, q2));
+    w.fh[2] = fma(2.0 / 3.0, d2, fma(-1.0 / 6.0, d3, q2));
+    w.fh[3] = fma(1.0 / 3.0, d4, fma(-5.0 / 6.0, d3, Q3D ? q2 + d2 : q3));
     w.e[0] = eps + b0;
     w.e[1] = eps + b1;
     w.e[2] = eps + b2;
@@ -327,6 +355,17 @@ struct FastMath {
   __device__ __forceinline__ static bool weno_front(const double* q, double eps, double alpha_R, double& out,
                                                     double* rec) {
     const double d0 = q[1] - q[0], d1 = q[2] - q[1], d2 = q[3] - q[2], d3 = q[4] - q[3], d4 = q[5] - q[4];
+    return weno_front_core<false>(d0, d1, d2, d3, d4, q[2], q[3], eps, alpha_R, out, rec);
+  }
+  // the same from the stencil's differences and q_2 (q_3 taken as q_2 + d_2)
+  __device__ __forceinline__ static bool weno_front_d(const double* d, double q2, double eps, double alpha_R,
+                                                      double& out, double* rec) {
+    return weno_front_core<true>(d[0], d[1], d[2], d[3], d[4], q2, 0.0, eps, alpha_R, out, rec);
+  }
+  template <bool Q3D>
+  __device__ __forceinline__ static bool weno_front_core(double d0, double d1, double d2, double d3, double d4,
+                                                         double q2, double q3, double eps, double alpha_R,
+                                                         double& out, double* rec) {
     const double s0 = d1 - d0, s1 = d2 - d1, s2 = d3 - d2, s3 = d4 - d3;
     const double t5b = s2 - s1;
     const double t5a = fma(-2.0, s1, s0) + s2;
@@ -334,13 +373,13 @@ struct FastMath {
     const double t6b = (s0 + s3) - (s1 + s2);
     const int scr = screen(s0, s1, s2, s3, d1, d2, d3, t5a, t5b, t6a, t6b, eps, alpha_R);
     if (scr != 0) {
-      out = linear_theta(d0, d1, d2, d3, d4, q[2], scr == 1);
+      out = linear_theta(d0, d1, d2, d3, d4, q2, scr == 1);
       return true;
     }
     rec[0] = d0; rec[1] = d1; rec[2] = d2; rec[3] = d3; rec[4] = d4;
     rec[5] = s0; rec[6] = s1; rec[7] = s2; rec[8] = s3;
     rec[9] = t5a; rec[10] = t5b; rec[11] = t6a; rec[12] = t6b;
-    rec[13] = q[2]; rec[14] = q[3];
+    rec[13] = q2; rec[14] = Q3D ? q2 + d2 : q3;
     return false;
   }
 
@@ -435,6 +474,11 @@ struct FastMath {
   __device__ __forceinline__ static double weno(const double* q, double eps, double alpha_R) {
     bool r, t;
     return weno_flags(q, eps, alpha_R, r, t);
+  }
+  __device__ __forceinline__ static double weno_d(const double* d, double q2, double eps, double alpha_R) {
+    WenoPart w;
+    double out;
+    return weno_begin_d(d, q2, eps, alpha_R, out, w) ? out : weno_finish(w);
   }
 
   __device__ __forceinline__ static void backproject(const double* rs, const double* F, double* h) {

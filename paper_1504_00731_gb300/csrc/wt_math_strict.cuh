@@ -15,6 +15,8 @@ struct StrictMath {
   static constexpr double kProj = 0.5, kLScale = 1.0;
   // the reconstruction is evaluated in one piece (weno_flags)
   static constexpr bool kSplitWeno = false;
+  // the projections are taken cell by cell, in the order of Eq. (flux_split_lf)
+  static constexpr bool kDiffProj = false;
   struct WenoPart {
     double e[4], tau, fh[4];
     bool theta1;
