@@ -128,6 +128,46 @@ __device__ __forceinline__ unsigned long long warp_max_key_redux(unsigned long l
   return ((unsigned long long)mh << 32) | ml;
 }
 
+// ---------------------------------------------------------------------------------------
+// FP32 screen of the 1D Euler wave speeds, so that a tile takes the FP64 speeds of only the
+// cells that can hold its maxima.  The FP64 maxima over those cells are the maxima over all.
+// ---------------------------------------------------------------------------------------
+
+// The high 32 bits of a double as a float: sign, exponent rebiased, the top 20 bits of the
+// mantissa, so |f32_hi(x) - x| < 2^-20 |x| for 2^-126 <= |x| < 2^128 (0 below).  Integer pipe.
+__device__ __forceinline__ float f32_hi(double x) {
+  const int hi = __double2hiint(x);
+  const int mag = hi & 0x7fffffff;
+  return mag < 0x38100000 ? 0.0f : __int_as_float(((mag - 0x38000000) << 3) | (hi & 0x80000000));
+}
+
+// lam = (|u - c|, |u|, |u + c|) of U = (rho, m, E) in FP32, g = gamma (gamma - 1) (a float
+// within 2^-20 of it).  Returns false, and leaves lam unset, unless rho and E lie in
+// [2^-60, 2^60], m is 0 or 2^-100 <= |m| <= 2^60, and the internal energy E - m u / 2 is at
+// least E / 16.  Otherwise, with d = 2^-20 (each input within d of its value) and every FP32
+// operation within 2^-22: 1 / rho within 1.1 d; u within 2.2 d of m / rho (relative, so
+// lam[1] is within 2.3 d of |u|); m u / 2 within 3.3 d, hence the internal energy within
+// 4.3 d E absolute, at most 69 d relative; c^2 = g (E - m u / 2) / rho within 71 d and c
+// within 36 d; so lam[0], lam[2] are within 37 d (|u| + c) < 2^-14.7 (|u| + c) of the exact
+// speeds.  The FP64 speeds are within a few 2^-53 of those.
+__device__ __forceinline__ bool euler_speeds_screen(const double* U, float g, float* lam) {
+  const float r = f32_hi(U[0]), m = f32_hi(U[1]), E = f32_hi(U[2]);
+  const float am = fabsf(m);
+  if (!(r >= 0x1p-60f && r <= 0x1p60f && E >= 0x1p-60f && E <= 0x1p60f && am <= 0x1p60f &&
+        (am >= 0x1p-100f || (__double_as_longlong(U[1]) << 1) == 0)))
+    return false;
+  const float ir = __frcp_rn(r);
+  const float u = m * ir;
+  const float pe = fmaf(-0.5f * m, u, E);
+  if (!(pe >= 0.0625f * E)) return false;
+  const float c2 = (g * pe) * ir;
+  const float c = c2 * rsqrtf(c2);
+  lam[0] = fabsf(u - c);
+  lam[1] = fabsf(u);
+  lam[2] = fabsf(u + c);
+  return true;
+}
+
 // Reduces K keys per thread to the block maximum and folds it into dst[k] with one
 // atomicMax per block.  scratch: >= K * 32 doubles of shared memory.
 template <int K>

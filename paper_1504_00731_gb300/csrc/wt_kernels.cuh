@@ -879,6 +879,14 @@ __device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long
   unsigned long long vmax[M];
 #pragma unroll
   for (int f = 0; f < M; ++f) vmax[f] = 0ull;
+  // Euler stage and resident tiles: the wave speeds of the stage output are screened in FP32
+  // (euler_speeds_screen) and kept in the dead buffer of the reconstructions (s_lam, +inf
+  // where the screen does not apply); the FP64 speeds are then taken only for the cells that
+  // can hold a maximum of the tile (below)
+  constexpr bool kScreen = FLUX == WT_FLUX_EULER1D && MODE != kStepBlocked && STAGE != STAGE_RHS;
+  float* s_lam = reinterpret_cast<float*>(s_F);
+  float m32[3] = {0.0f, 0.0f, 0.0f};
+  const float g32 = f32_hi(a.gamma * (a.gamma - 1.0));
   for (int t = tid; t < Tc; t += NT) {
     const long long j = js + t;
     const bool own = (MODE != kStepBlocked) || (j >= own_lo && j < own_hi);
@@ -927,7 +935,21 @@ __device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long
       if (own && MODE == kStepBlocked) {
         if (FLUX == WT_FLUX_EULER1D ? !finite3(uo) : !isfinite(uo[0])) flag_error(ctl, WT_ERR_NONPHYSICAL);
       } else if (own) {
-        if (FLUX == WT_FLUX_EULER1D) {
+        if constexpr (kScreen) {
+          if (!finite3(uo)) flag_error(ctl, WT_ERR_NONPHYSICAL);
+          float l32[3];
+          const bool ok = euler_speeds_screen(uo, g32, l32);
+#pragma unroll
+          for (int f = 0; f < 3; ++f) {
+            s_lam[f * NI + t] = ok ? l32[f] : INFINITY;
+            if (ok) m32[f] = fmaxf(m32[f], l32[f]);
+          }
+          // the FP64 pass reads the output back (resident tiles hold it there already)
+          if (MODE == kStage) {
+#pragma unroll
+            for (int c = 0; c < M; ++c) s_uin[c * W + off + t + G] = uo[c];
+          }
+        } else if (FLUX == WT_FLUX_EULER1D) {
           double lam[3];
           MATH::euler_speeds(uo, a.gamma, lam);
           if (!finite3(uo)) flag_error(ctl, WT_ERR_NONPHYSICAL);
@@ -937,6 +959,55 @@ __device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long
           const double lam = (FLUX == WT_FLUX_ADVECTION) ? fabs(a.adv_speed) : fabs(uo[0]);
           if (!isfinite(uo[0])) flag_error(ctl, WT_ERR_NONPHYSICAL);
           key_max(vmax[0], lam);
+        }
+      }
+    }
+  }
+  if constexpr (kScreen) {
+    // The tile's FP32 maxima m_s.  With e = 2^-14.6 max(m_0, m_2) bounding every cell's error
+    // in lam_0, lam_2 (|u| + c <= max(lam_0, lam_2) + its error), a cell holding the FP64
+    // maximum of field 0 or 2 has lam_s >= m_s - 2 e; for field 1 (no cancellation, error
+    // 2.3 * 2^-20 relative) lam_1 >= m_1 (1 - 2^-17.8), and where m_1 = 0 every screened cell
+    // has m = 0, |u| = 0 exactly.  Margins 2^-12 and 2^-16 are taken.  A candidate for field 1
+    // only takes |u| (MATH::speed_u), one for field 0 or 2 the sound speed as well; a cell whose
+    // state equals its left neighbour's bit for bit has the same speeds and is skipped (a run
+    // of equal states is decided by its first cell, which has the same screen values).
+    float* s_lm = s_lam + 3 * NI;  // [3][32] warp maxima
+    const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+      float v = m32[f];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+      if (lane == 0) s_lm[f * 32 + warp] = v;
+    }
+    __syncthreads();
+    float tm[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int f = 0; f < 3; ++f)
+      for (int w = 0; w < NT / 32; ++w) tm[f] = fmaxf(tm[f], s_lm[f * 32 + w]);
+    const float smx = fmaxf(tm[0], tm[2]);
+    const float thr0 = tm[0] - 0x1p-12f * smx, thr2 = tm[2] - 0x1p-12f * smx;
+    const float thr1 = tm[1] * (1.0f - 0x1p-16f);
+    for (int t = tid; t < Tc; t += NT) {
+      const float l0 = s_lam[t], l1 = s_lam[NI + t], l2 = s_lam[2 * NI + t];
+      const bool c02 = l0 >= thr0 || l2 >= thr2;
+      if (c02 || (l1 > 0.0f && l1 >= thr1)) {
+        const int k = off + t + G;
+        double U[3] = {s_uin[k], s_uin[W + k], s_uin[2 * W + k]};
+        bool dup = t > 0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          dup = dup && __double_as_longlong(U[c]) == __double_as_longlong(s_uin[c * W + k - 1]);
+        if (!dup) {
+          double u, ir;
+          key_max(vmax[1], MATH::speed_u(U, u, ir));
+          if (c02) {
+            double a0, a2;
+            MATH::speed_c(U, a.gamma, u, ir, a0, a2);
+            key_max(vmax[0], a0);
+            key_max(vmax[2], a2);
+          }
         }
       }
     }

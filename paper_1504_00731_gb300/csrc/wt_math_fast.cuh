@@ -82,6 +82,22 @@ struct FastMath {
     return p;
   }
 
+  // euler_speeds in two parts, with its operations: |u| (keeping u and 1 / rho), then
+  // |u - c| and |u + c|
+  __device__ __forceinline__ static double speed_u(const double* U, double& u, double& ir) {
+    const double r = rsqrt(U[0]);
+    ir = r * r;
+    u = U[1] * ir;
+    return fabs(u);
+  }
+  __device__ __forceinline__ static void speed_c(const double* U, double gamma, double u, double ir, double& l0,
+                                                 double& l2) {
+    const double p = (gamma - 1.0) * fma(-0.5 * U[1], u, U[2]);
+    const double c = sound_speed(gamma * p * ir);
+    l0 = fabs(u - c);
+    l2 = fabs(u + c);
+  }
+
   // L is stored pre-scaled by 1/2 (the factor of Eq. (flux_split_lf))
   __device__ __forceinline__ static void roe(double sa, double ua, double Ha, double sb, double ub, double Hb,
                                              double gamma, double* L, double* rs) {

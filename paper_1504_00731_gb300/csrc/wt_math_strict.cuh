@@ -63,6 +63,20 @@ struct StrictMath {
     return p;
   }
 
+  // euler_speeds in two parts, with its operations: |u| (keeping u), then |u - c| and |u + c|
+  __device__ __forceinline__ static double speed_u(const double* U, double& u, double& ir) {
+    u = U[1] / U[0];
+    ir = 0.0;
+    return fabs(u);
+  }
+  __device__ __forceinline__ static void speed_c(const double* U, double gamma, double u, double, double& l0,
+                                                 double& l2) {
+    double p = (gamma - 1.0) * (U[2] - 0.5 * U[0] * u * u);
+    double c = sqrt(gamma * p / U[0]);
+    l0 = fabs(u - c);
+    l2 = fabs(u + c);
+  }
+
   // ---- Roe's mean state between two cells and the left eigenvectors L (row-major 3x3)
   //      of Roe's matrix; rs = (u~, H~, c~) for the right eigenvectors.
   __device__ __forceinline__ static void roe(double sa, double ua, double Ha, double sb, double ub, double Hb,
