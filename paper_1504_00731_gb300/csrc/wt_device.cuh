@@ -128,6 +128,12 @@ __device__ __forceinline__ unsigned long long warp_max_key_redux(unsigned long l
   return ((unsigned long long)mh << 32) | ml;
 }
 
+// x with its sign bit XORed with that of sg (0 or -0.0's pattern): an exact negation on the
+// integer pipe
+__device__ __forceinline__ double flip_sign(double x, unsigned long long sg) {
+  return __longlong_as_double((long long)((unsigned long long)__double_as_longlong(x) ^ sg));
+}
+
 // ---------------------------------------------------------------------------------------
 // FP32 screen of the 1D Euler wave speeds, so that a tile takes the FP64 speeds of only the
 // cells that can hold its maxima.  The FP64 maxima over those cells are the maxima over all.

@@ -47,10 +47,12 @@ struct Tile1D {
   static constexpr int kHf = LATE ? kL : kFs + 2 * M * NI;
   static constexpr int kUn = LATE ? kL + M * NI : kUin + M * W;
   static_assert(!LATE || (M * NI + M * W <= 9 * NI && (kUn % 2) == 0), "h and u^n fit the eigenvector buffer");
-  static constexpr int kDf = kVel;                // DP: [M][W] f_{k+1} - f_k
+  // (step-blocked tiles, one per SM: f's differences get planes of their own and are taken
+  // during phase C0)
   static constexpr int kDu = LATE ? kFs + 2 * M * NI : kHf + M * NI;  // DP: [M][W] u_{k+1} - u_k
+  static constexpr int kDf = SPLIT == 2 ? kDu + M * W : kVel;         // DP: [M][W] f_{k+1} - f_k
   static_assert(!DP || M == 3, "differences first: 1D Euler tiles");
-  static constexpr int kRed = kDu + (DP ? M * W : 0);
+  static constexpr int kRed = kDu + (DP ? (SPLIT == 2 ? 2 : 1) * M * W : 0);
   static constexpr int kQn = kRed + 4 * 32;      // queue length (int)
   // queue of reconstructions still to be completed: one slot per thread, fewer if the tile
   // would pass 48 KB (the rest are completed in place).  A record holds the weights' inputs
@@ -414,13 +416,26 @@ __device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long
 #pragma unroll
       for (int e = 0; e < 3; ++e) s_rs[e * NI + i] = rs[e];
     }
+    if constexpr (DP && MODE == kStepBlocked) {
+      // differences k = i + 2 by the thread of interface i, the four outer ones (k = 0, 1,
+      // Tc + 3, Tc + 4) by the next four threads; ni + 4 <= NT - 32 (static_assert below)
+      const int k = tid < ni ? tid + 2 : (tid < ni + 2 ? tid - ni : Tc + 3 + (tid - ni - 2));
+      if (tid < ni + 4) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          sm[TL::kDf + c * W + k] = s_f[c * W + k + 1] - s_f[c * W + k];
+          sm[TL::kDu + c * W + k] = s_uin[c * W + off + k + 1] - s_uin[c * W + off + k];
+        }
+      }
+    }
     c0_barrier();
   }
+  static_assert(!(DP && MODE == kStepBlocked) || NI + 4 <= NT - 32, "outer differences fit the C0 threads");
   // DP: the differences of f and u between neighbouring window cells (f's over the per-cell
   // Roe inputs, read for the last time in phase C0), by the threads of phase C0
   double* s_df = sm + TL::kDf;
   double* s_du = sm + TL::kDu;
-  if constexpr (DP) {
+  if constexpr (DP && MODE != kStepBlocked) {
     if (!(sw_free && (tid >> 5) == kSW)) {
       const int np = sw_free ? NT - 32 : NT;
       for (int k = tid; k < cells - 1; k += np) {
@@ -479,21 +494,22 @@ __device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long
       double p[6];
 #pragma unroll
       for (int r = 0; r < 6; ++r) p[r] = __shfl_xor_sync(0xffffffffu, o[r], 1);
-      const bool mi = side2 != 0;
-      a2 = mi ? p[0] : o[0];
-      b2 = mi ? p[1] : o[1];
-      a3 = mi ? o[0] : p[0];
-      b3 = mi ? o[1] : p[1];
-      da[0] = mi ? p[2] : o[2];
-      db[0] = mi ? p[3] : o[3];
-      da[1] = mi ? p[4] : o[4];
-      db[1] = mi ? p[5] : o[5];
-      da[4] = mi ? o[2] : p[2];
-      db[4] = mi ? o[3] : p[3];
-      da[3] = mi ? o[4] : p[4];
-      db[3] = mi ? o[5] : p[5];
-      da[2] = a3 - a2;
-      db[2] = b3 - b2;
+      // the side's stencil order: its own products are differences 0, 1 (+ side) or 4, 3
+      // (- side, mirrored), its partner's the other two in reverse, and difference 2 is
+      // a3 - a2 on both sides (the partner's centre minus its own, negated on the - side)
+      const unsigned long long sg = side2 ? 0x8000000000000000ull : 0ull;
+      da[0] = o[2];
+      db[0] = o[3];
+      da[1] = o[4];
+      db[1] = o[5];
+      da[4] = p[2];
+      db[4] = p[3];
+      da[3] = p[4];
+      db[3] = p[5];
+      da[2] = flip_sign(p[0] - o[0], sg);
+      db[2] = flip_sign(p[1] - o[1], sg);
+      a2 = o[0];  // the own centre cell's products
+      b2 = o[1];
     }
   } else if constexpr (DP) {
     if (has_item && IPT == 1) {
@@ -622,20 +638,22 @@ __device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long
   };
   if constexpr (DP) {
     // differences first: the reconstructions from their stencils' differences and q_2
-    auto reconstruct_d = [&](const double* d, const double q2, const int dst) {
+    // (step-blocked: sg negates the result of a - side thread, which reconstructs its stencil
+    // negated; its queue record carries bit 30)
+    auto reconstruct_d = [&](const double* d, const double q2, const int dst, const unsigned long long sg = 0ull) {
       double out;
       if constexpr (MODE == kStepBlocked) {
         double rec[TL::REC];
         if (MATH::weno_front_d(d, q2, a.eps, a.alpha_R, out, rec)) {
-          s_F[dst] = out;
+          s_F[dst] = flip_sign(out, sg);
         } else {
           const int slot = atomicAdd(s_qn, 1);
           if (slot < QCAP) {
 #pragma unroll
             for (int r = 0; r < TL::REC; ++r) s_q[r * QCAP + slot] = rec[r];
-            s_qi[slot] = dst;
+            s_qi[slot] = dst | (sg ? (1 << 30) : 0);
           } else {
-            s_F[dst] = MATH::weno_d(d, q2, a.eps, a.alpha_R);
+            s_F[dst] = flip_sign(MATH::weno_d(d, q2, a.eps, a.alpha_R), sg);
           }
         }
       } else {
@@ -683,8 +701,17 @@ __device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long
       const double al = (s == 0) ? alpha[0] : ((s == 1) ? alpha[1] : alpha[M - 1]);
       double d[5], q2;
       if constexpr (SPLIT == 2) {
-        MATH::side_diffs(da, db, a2, b2, a3, b3, al, side2 != 0, d, q2);
-        reconstruct_d(d, q2, side2 * (M * NI) + s * NI + i);
+        // The - side reconstructs its stencil negated: the reconstruction is odd in its data bit
+        // for bit (squares and comparisons do not see the sign; every other step is a rounded
+        // linear operation, and round-to-nearest is symmetric), so -weno(-d, -q2) is the value
+        // of MATH::side_diffs' stencil.  Its differences are then alpha-combined like the + side's,
+        // with -alpha, from the side-ordered products, and no selects are needed.
+        const unsigned long long sg = side2 ? 0x8000000000000000ull : 0ull;
+        const double sa = flip_sign(al, sg);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) d[k] = fma(sa, db[k], da[k]);
+        q2 = fma(al, b2, flip_sign(a2, sg));  // + side: a2 + alpha b2; - side: alpha b3 - a3
+        reconstruct_d(d, q2, side2 * (M * NI) + s * NI + i, sg);
       } else {
         MATH::side_diffs(da, db, a2, b2, a3, b3, al, false, d, q2);
         reconstruct_d(d, q2, s * NI + i);
@@ -768,7 +795,8 @@ __device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long
           for (int r = 0; r < TL::REC; ++r) rec[r] = s_q[r * QCAP + t];
           const unsigned qmask = 0xfu << (tid & 28);
           const double out = MATH::weno_back_quad(k, rec, a.eps, a.alpha_R, qmask);
-          if (k == 0) s_F[s_qi[t]] = out;
+          const int qi = s_qi[t];  // bit 30: a negated - side stencil
+          if (k == 0) s_F[qi & ((1 << 30) - 1)] = flip_sign(out, (qi >> 30) & 1 ? 0x8000000000000000ull : 0ull);
         }
       }
       __syncthreads();
