@@ -158,12 +158,15 @@ __device__ __forceinline__ void euler_uc_grad(const double* U, double gamma, dou
 
 // Reverse of Roe's average and the eigenvectors: true Lbar (3x3) and Rbar (3x3, R[c][s]) of
 // the interface between cells a and b -> Ubar_a, Ubar_b.
+// ira, irb: 1 / rho of the two cells.
 __device__ __forceinline__ void roe_reverse(const double* Ua, const double* Ub, double sa, double ua, double Ha,
-                                            double sb, double ub, double Hb, const double* rs, double gamma,
-                                            const double* Lb, const double* Rb, double* Uab, double* Ubb) {
-  // reciprocals once (an IEEE division costs about nine FMA slots of the narrow FP64 pipe)
+                                            double ira, double sb, double ub, double Hb, double irb, const double* rs,
+                                            double gamma, const double* Lb, const double* Rb, double* Uab,
+                                            double* Ubb) {
+  // reciprocals from square roots (an IEEE division costs about nine FMA slots of the narrow
+  // FP64 pipe): 1 / c from c^2 = (gamma - 1)(H - u^2 / 2), and the cells' 1 / rho given
   const double u = rs[0], H = rs[1], c = rs[2], gm1 = gamma - 1.0;
-  const double ic = 1.0 / c, ic2 = ic * ic;
+  const double ic = rsqrt(gm1 * fma(-0.5 * u, u, H)), ic2 = ic * ic;
   const double b1 = gm1 * ic2;
   double ubar = 0, cbar = 0, Hbar = 0, b1b = 0, b2b = 0, r1b = 0, r2b = 0;
   b2b += 0.5 * Lb[0];
@@ -203,13 +206,13 @@ __device__ __forceinline__ void roe_reverse(const double* Ua, const double* Ub, 
   const double sbb = (ubar * (ub - u) + Hbar * (Hb - H)) * iD;
   // per cell: u = m / rho, H = gamma E / rho - (gamma - 1) u^2 / 2, s = sqrt(rho); 1/s = s / rho
   {
-    const double ir = 1.0 / Ua[0], E = Ua[2];
+    const double ir = ira, E = Ua[2];
     Uab[0] += uab * (-ua * ir) + Hab * ((-gamma * E * ir + gm1 * ua * ua) * ir) + 0.5 * sab * sa * ir;
     Uab[1] += uab * ir + Hab * (-gm1 * ua * ir);
     Uab[2] += Hab * gamma * ir;
   }
   {
-    const double ir = 1.0 / Ub[0], E = Ub[2];
+    const double ir = irb, E = Ub[2];
     Ubb[0] += ubb * (-ub * ir) + Hbb * ((-gamma * E * ir + gm1 * ub * ub) * ir) + 0.5 * sbb * sb * ir;
     Ubb[1] += ubb * ir + Hbb * (-gm1 * ub * ir);
     Ubb[2] += Hbb * gamma * ir;
@@ -234,7 +237,8 @@ struct AdjTile {
   static constexpr int kVel = kF + M * W;
   static constexpr int kH = kVel + W;
   static constexpr int kSr = kH + W;
-  static constexpr int kL = kSr + W;         // [9][NI] stored L
+  static constexpr int kIr = kSr + W;        // 1 / rho per cell
+  static constexpr int kL = kIr + W;         // [9][NI] stored L
   static constexpr int kRs = kL + 9 * NI;    // [3][NI]
   static constexpr int kFs = kRs + 3 * NI;   // [3][NI] F_s = F+ + F-
   static constexpr int kHf = kFs + 3 * NI;   // [3][NI] h
@@ -272,6 +276,7 @@ __global__ void __launch_bounds__(AdjTile<T, IPT>::NT) adj_stage_kernel(const Ad
   double* s_vel = sm + TL::kVel;
   double* s_H = sm + TL::kH;
   double* s_sr = sm + TL::kSr;
+  double* s_ir = sm + TL::kIr;
   double* s_L = sm + TL::kL;
   double* s_rs = sm + TL::kRs;
   double* s_F = sm + TL::kFs;
@@ -334,6 +339,8 @@ __global__ void __launch_bounds__(AdjTile<T, IPT>::NT) adj_stage_kernel(const Ad
       s_vel[k] = u;
       s_H[k] = H;
       s_sr[k] = sr;
+      const double r = rsqrt(U[0]);
+      s_ir[k] = r * r;  // for the reverse Roe average (two per interface), one per cell
     }
     __syncthreads();
     // ---- C0: per interface (local li: cells li+2 | li+3; global interface j0 - 1 + li, record
@@ -377,24 +384,18 @@ __global__ void __launch_bounds__(AdjTile<T, IPT>::NT) adj_stage_kernel(const Ad
       const unsigned fl = s_flags[i];
       const bool rp = (fl >> (2 * s)) & 1u, tp = (fl >> (2 * s + 1)) & 1u;
       const bool rm = (fl >> (2 * (3 + s))) & 1u, tm = (fl >> (2 * (3 + s) + 1)) & 1u;
-      double vp[6] = {0, 0, 0, 0, 0, 0}, qm[6] = {0, 0, 0, 0, 0, 0}, pb[6];
-      if (rp && rm) {
-#pragma unroll
-        for (int kk = 0; kk < 6; ++kk) {
-          const int k = i + kk;
-          const double U[3] = {s_uin[off + k], s_uin[W + off + k], s_uin[2 * W + off + k]};
-          pb[kk] = MATH::project3_b(l, U);
-        }
-      } else {
+      // only a stencil that was not restricted needs its projected values (weno_grad)
+      double vp[6] = {0, 0, 0, 0, 0, 0}, qm[6] = {0, 0, 0, 0, 0, 0};
+      if (!(rp && rm)) {
         double vm[6];
 #pragma unroll
         for (int kk = 0; kk < 6; ++kk) {
           const int k = i + kk;
           const double f[3] = {s_f[k], s_f[W + k], s_f[2 * W + k]};
           const double U[3] = {s_uin[off + k], s_uin[W + off + k], s_uin[2 * W + off + k]};
-          double pa;
-          MATH::project3_ab(l, f, U, pa, pb[kk]);  // the same operations as project3
-          MATH::project_v(pa, pb[kk], al[s], vp[kk], vm[kk]);
+          double pa, pb;
+          MATH::project3_ab(l, f, U, pa, pb);  // the same operations as project3
+          MATH::project_v(pa, pb, al[s], vp[kk], vm[kk]);
         }
 #pragma unroll
         for (int kk = 0; kk < 6; ++kk) qm[kk] = vm[5 - kk];
@@ -411,27 +412,30 @@ __global__ void __launch_bounds__(AdjTile<T, IPT>::NT) adj_stage_kernel(const Ad
       double vpb[6] = {0, 0, 0, 0, 0, 0}, qmb[6] = {0, 0, 0, 0, 0, 0};
       weno_grad(vp, a.eps, rp, tp, Fb, vpb);
       weno_grad(qm, a.eps, rm, tm, Fb, qmb);
-      double Lb3[3] = {0, 0, 0};
-      double ab_alpha = 0.0;
+      // With s_k = v+bar_k + v-bar_k and d_k = v+bar_k - v-bar_k (v-bar mirrored), the stored
+      // L row's adjoint is kProj (Sf + alpha Su), Sf = sum_k s_k f_k, Su = sum_k d_k u_k, and
+      // d/d alpha is kProj l.Su: one pass over the stencil for both
+      double Sf[3] = {0, 0, 0}, Su[3] = {0, 0, 0};
 #pragma unroll
       for (int kk = 0; kk < 6; ++kk) {
         const int k = i + kk;
         const double f[3] = {s_f[k], s_f[W + k], s_f[2 * W + k]};
         const double U[3] = {s_uin[off + k], s_uin[W + off + k], s_uin[2 * W + off + k]};
         const double vmb = qmb[5 - kk];
-        const double bq = pb[kk];  // stored-L projection of u
-        const double abk = MATH::kProj * (vpb[kk] + vmb);
-        const double bbk = MATH::kProj * al[s] * (vpb[kk] - vmb);
-        ab_alpha = fma(MATH::kProj * bq, vpb[kk] - vmb, ab_alpha);
+        const double sk = vpb[kk] + vmb, dk = vpb[kk] - vmb;
 #pragma unroll
-        for (int e = 0; e < 3; ++e) Lb3[e] = fma(abk, f[e], fma(bbk, U[e], Lb3[e]));
+        for (int e = 0; e < 3; ++e) {
+          Sf[e] = fma(sk, f[e], Sf[e]);
+          Su[e] = fma(dk, U[e], Su[e]);
+        }
         // adjoints of the projected flux and state of stencil cell kk; phase D reverse forms
         // their images under the three fields' L rows
-        Gs[kk] = abk;
-        Gs[6 + kk] = bbk;
+        Gs[kk] = MATH::kProj * sk;
+        Gs[6 + kk] = MATH::kProj * al[s] * dk;
       }
 #pragma unroll
-      for (int e = 0; e < 3; ++e) Lbs[e] = Lb3[e];
+      for (int e = 0; e < 3; ++e) Lbs[e] = MATH::kProj * fma(al[s], Su[e], Sf[e]);
+      const double ab_alpha = MATH::kProj * MATH::project3_b(l, Su);
       if (s == 0) abar0 += ab_alpha;
       else if (s == 1) abar1 += ab_alpha;
       else abar2 += ab_alpha;
@@ -476,7 +480,8 @@ __global__ void __launch_bounds__(AdjTile<T, IPT>::NT) adj_stage_kernel(const Ad
       const double Ua[3] = {s_uin[off + ka], s_uin[W + off + ka], s_uin[2 * W + off + ka]};
       const double Ubv[3] = {s_uin[off + kb], s_uin[W + off + kb], s_uin[2 * W + off + kb]};
       double Uab[3] = {0, 0, 0}, Ubb[3] = {0, 0, 0};
-      roe_reverse(Ua, Ubv, s_sr[ka], s_vel[ka], s_H[ka], s_sr[kb], s_vel[kb], s_H[kb], rs, a.gamma, Lb, Rb, Uab, Ubb);
+      roe_reverse(Ua, Ubv, s_sr[ka], s_vel[ka], s_H[ka], s_ir[ka], s_sr[kb], s_vel[kb], s_H[kb], s_ir[kb], rs, a.gamma,
+                  Lb, Rb, Uab, Ubb);
       const long long gi = j0 - 1 + i;
       double* out = a.G + (a.goff[p] + gi + 1) * 36;
       // the stencil cells' flux and state adjoints: sum over the fields s of ab_s l_s, bb_s l_s
