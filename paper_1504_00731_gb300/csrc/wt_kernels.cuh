@@ -47,12 +47,12 @@ struct Tile1D {
   static constexpr int kHf = LATE ? kL : kFs + 2 * M * NI;
   static constexpr int kUn = LATE ? kL + M * NI : kUin + M * W;
   static_assert(!LATE || (M * NI + M * W <= 9 * NI && (kUn % 2) == 0), "h and u^n fit the eigenvector buffer");
-  // (step-blocked tiles, one per SM: f's differences get planes of their own and are taken
-  // during phase C0)
+  // (resident and step-blocked tiles, latency-bound: f's differences get planes of their own
+  // and are taken during phase C0)
   static constexpr int kDu = LATE ? kFs + 2 * M * NI : kHf + M * NI;  // DP: [M][W] u_{k+1} - u_k
-  static constexpr int kDf = SPLIT == 2 ? kDu + M * W : kVel;         // DP: [M][W] f_{k+1} - f_k
+  static constexpr int kDf = LATE ? kVel : kDu + M * W;               // DP: [M][W] f_{k+1} - f_k
   static_assert(!DP || M == 3, "differences first: 1D Euler tiles");
-  static constexpr int kRed = kDu + (DP ? (SPLIT == 2 ? 2 : 1) * M * W : 0);
+  static constexpr int kRed = kDu + (DP ? (LATE ? 1 : 2) * M * W : 0);
   static constexpr int kQn = kRed + 4 * 32;      // queue length (int)
   // queue of reconstructions still to be completed: one slot per thread, fewer if the tile
   // would pass 48 KB (the rest are completed in place).  A record holds the weights' inputs
@@ -416,9 +416,10 @@ __device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long
 #pragma unroll
       for (int e = 0; e < 3; ++e) s_rs[e * NI + i] = rs[e];
     }
-    if constexpr (DP && MODE == kStepBlocked) {
+    if constexpr (DP && MODE != kStage) {
       // differences k = i + 2 by the thread of interface i, the four outer ones (k = 0, 1,
-      // Tc + 3, Tc + 4) by the next four threads; ni + 4 <= NT - 32 (static_assert below)
+      // Tc + 3, Tc + 4) by the next four threads, none of them the speed warp (static_assert
+      // below)
       const int k = tid < ni ? tid + 2 : (tid < ni + 2 ? tid - ni : Tc + 3 + (tid - ni - 2));
       if (tid < ni + 4) {
 #pragma unroll
@@ -430,12 +431,13 @@ __device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long
     }
     c0_barrier();
   }
-  static_assert(!(DP && MODE == kStepBlocked) || NI + 4 <= NT - 32, "outer differences fit the C0 threads");
+  static_assert(!DP || MODE == kStage || NI + 4 <= NT - (MODE == kStepBlocked ? 32 : 0),
+                "outer differences fit the C0 threads");
   // DP: the differences of f and u between neighbouring window cells (f's over the per-cell
   // Roe inputs, read for the last time in phase C0), by the threads of phase C0
   double* s_df = sm + TL::kDf;
   double* s_du = sm + TL::kDu;
-  if constexpr (DP && MODE != kStepBlocked) {
+  if constexpr (DP && MODE == kStage) {
     if (!(sw_free && (tid >> 5) == kSW)) {
       const int np = sw_free ? NT - 32 : NT;
       for (int k = tid; k < cells - 1; k += np) {
@@ -907,11 +909,11 @@ __device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long
   unsigned long long vmax[M];
 #pragma unroll
   for (int f = 0; f < M; ++f) vmax[f] = 0ull;
-  // Euler stage and resident tiles: the wave speeds of the stage output are screened in FP32
+  // Euler stage tiles (throughput-bound): the wave speeds of the stage output are screened in FP32
   // (euler_speeds_screen) and kept in the dead buffer of the reconstructions (s_lam, +inf
   // where the screen does not apply); the FP64 speeds are then taken only for the cells that
   // can hold a maximum of the tile (below)
-  constexpr bool kScreen = FLUX == WT_FLUX_EULER1D && MODE != kStepBlocked && STAGE != STAGE_RHS;
+  constexpr bool kScreen = FLUX == WT_FLUX_EULER1D && MODE == kStage && STAGE != STAGE_RHS;
   float* s_lam = reinterpret_cast<float*>(s_F);
   float m32[3] = {0.0f, 0.0f, 0.0f};
   const float g32 = f32_hi(a.gamma * (a.gamma - 1.0));
@@ -972,11 +974,9 @@ __device__ __forceinline__ bool stage1d_compute(const Stage1DArgs& a, const long
             s_lam[f * NI + t] = ok ? l32[f] : INFINITY;
             if (ok) m32[f] = fmaxf(m32[f], l32[f]);
           }
-          // the FP64 pass reads the output back (resident tiles hold it there already)
-          if (MODE == kStage) {
+          // the FP64 pass reads the output back
 #pragma unroll
-            for (int c = 0; c < M; ++c) s_uin[c * W + off + t + G] = uo[c];
-          }
+          for (int c = 0; c < M; ++c) s_uin[c * W + off + t + G] = uo[c];
         } else if (FLUX == WT_FLUX_EULER1D) {
           double lam[3];
           MATH::euler_speeds(uo, a.gamma, lam);
@@ -1203,7 +1203,7 @@ __device__ __forceinline__ void load_halos(const double* uin, long long pitch, l
 }
 
 template <class MATH, int FLUX, int T>
-__global__ void __launch_bounds__(Tile1D<T, FluxM<FLUX>::m>::NT) persist1d_kernel(const PersistArgs p) {
+__global__ void __launch_bounds__(Tile1D<T, FluxM<FLUX>::m>::NT, 3) persist1d_kernel(const PersistArgs p) {
   constexpr int M = FluxM<FLUX>::m;
   using TL = TileOf<MATH, FLUX, T>;
   constexpr int W = TL::W, NT = TL::NT;
