@@ -175,6 +175,10 @@ int weno_theta_step(const wt_problem* prob, const wt_grid* grid, double* u, doub
  * depend on the choice.  The environment variable WT_BATCHED_TILE, if set, fixes the choice to
  * one tile code (cells per tile + 1000 x (items per thread - 1); Euler: 31, 63, 127, 1063,
  * 1127, 2127, 3127, 5127; scalar fluxes: 63, 127), for tests and for callers that tuned offline.
+ * Host arrays: with u_packed in page-locked host memory, segments laid out in the order of the
+ * problems, at least 2^23 cells and the tile already chosen, the call runs in up to four chunks
+ * of problems, so that one chunk's copies to and from the device overlap another's steps (the
+ * results are the same bit for bit; on failure the input is put back as described above).
  * Synchronises `stream` before returning.
  */
 int weno_theta_step_batched(const wt_problem* prob, const wt_segment* segs, int32_t nprob, double* u_packed,

@@ -191,6 +191,17 @@ int pointer_info(const void* p, bool* is_device, int* device) {
   return WT_OK;
 }
 
+// Host memory the driver has page-locked (or registered): asynchronous copies from and to it
+// overlap kernels; copies of pageable memory do not.
+bool pinned_host(const void* p) {
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return attr.type == cudaMemoryTypeHost;
+}
+
 // Makes the workspace's device current for the duration of a call.
 struct DeviceGuard {
   int old = -1;
@@ -250,6 +261,7 @@ struct GraphEntry {
 std::mutex g_graph_mu;
 std::vector<GraphEntry> g_graphs;
 cudaStream_t g_capture_stream[64] = {};
+cudaStream_t g_copy_stream[64][2] = {};  // per device: copies to the device, copies back
 
 bool same_args(const Stage1DArgs& x, const Stage1DArgs& y) { return memcmp(&x, &y, sizeof x) == 0; }
 
@@ -332,7 +344,7 @@ int tile_candidates(int flux, int* out) {
 }
 
 struct BatchLayout {
-  size_t ctl, segs, tiles, un, u1, u2, st_u, st_t, total;
+  size_t ctl, segs, tiles, un, u1, u2, st_u, st_o, st_t, total;
   long long pitch;
   long long max_tiles;
 };
@@ -356,6 +368,8 @@ BatchLayout layout_batched(int m, int nprob, long long pitch, long long max_tile
   L.u2 = o;
   o = align_up(o + plane);
   L.st_u = o;
+  o = align_up(o + sizeof(double) * (size_t)m * total_cells);
+  L.st_o = o;  // results of a pipelined host call (the input stays in st_u until the call ends)
   o = align_up(o + sizeof(double) * (size_t)m * total_cells);
   L.st_t = o;
   o = align_up(o + sizeof(double) * (size_t)nprob);
@@ -979,6 +993,188 @@ int weno_theta_step(const wt_problem* prob, const wt_grid* grid, double* u, doub
   return finish_step_1d(ctl, Un, lay, u, u_dev, st_in, m, n, t_reached, steps, st);
 }
 
+// Chunks of a pipelined host call (step_batched_pipelined): host arrays the driver has
+// page-locked, segments laid out in the order of the problems (so each chunk's part of the
+// caller's array is one range) and at least 2^22 cells per chunk; at most four.  1: none.
+int pipeline_chunks(const wt_segment* segs, int nprob, long long cells, const double* u) {
+  int k = (int)std::min<long long>(4, cells >> 22);
+  if (k > nprob) k = nprob;
+  if (k < 2) return 1;
+  for (int p = 1; p < nprob; ++p)
+    if (segs[p].offset < segs[p - 1].offset + segs[p - 1].n) return 1;
+  return pinned_host(u) ? k : 1;
+}
+
+// Events of one call, destroyed on every way out
+struct EventSet {
+  std::vector<cudaEvent_t> e;
+  cudaError_t make(int n) {
+    e.assign(n, nullptr);
+    for (auto& x : e) {
+      const cudaError_t r = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
+      if (r != cudaSuccess) return r;
+    }
+    return cudaSuccess;
+  }
+  ~EventSet() {
+    for (auto x : e)
+      if (x) cudaEventDestroy(x);
+  }
+};
+
+// A batched call on host arrays in chunks of problems: per chunk, the copy of its part of the
+// caller's array to the device (first copy stream); then, on the call's stream, the boundary
+// fill, its alphas, the RK steps (a graph of the three stage launches over the chunk's part of
+// the tile table) and the unpacking into the result buffer; then the copy back (second copy
+// stream).  One chunk's copies overlap another's steps.  The chunks run the same kernels on
+// subsets of problems that share nothing, so every problem's result is bit for bit that of one
+// launch over all of them.  The input stays in st_u until the call ends: a failure restores
+// it (all of u without a status array, the failed problems' parts with one).
+int step_batched_pipelined(const wt_problem* prob, const wt_segment* segs, int nprob, double* u, int64_t total,
+                           int64_t n_steps, double* t_out, bool t_dev, int32_t* s_out, bool s_dev,
+                           const std::vector<BatchSeg>& hs, const std::vector<Ctl>& hctl, long long pitch, int tile,
+                           int nchunk, int dev, Ctl* ctl, BatchSeg* dsegs, int2* dtiles, double* Un, double* U1,
+                           double* U2, double* st_u, double* st_o, cudaStream_t st) {
+  const int m = prob->m;
+  long long cells = 0;
+  for (const auto& h : hs) cells += h.n;
+  // chunk boundaries: about equal cells, none empty
+  std::vector<int> cb(1, 0);
+  long long acc = 0;
+  for (int p = 0; p + 1 < nprob; ++p) {
+    acc += hs[p].n;
+    if ((int)cb.size() < nchunk && acc * nchunk >= (long long)cb.size() * cells) cb.push_back(p + 1);
+  }
+  cb.push_back(nprob);
+  const int K = (int)cb.size() - 1;
+  // the chunks' tile tables one after another (problem indices local to the chunk)
+  std::vector<int2> tl;
+  std::vector<long long> tb(K + 1, 0);
+  for (int c = 0; c < K; ++c) {
+    const std::vector<BatchSeg> sub(hs.begin() + cb[c], hs.begin() + cb[c + 1]);
+    const std::vector<int2> t = make_tiles(sub, tile);
+    tl.insert(tl.end(), t.begin(), t.end());
+    tb[c + 1] = (long long)tl.size();
+  }
+  WT_CUDA(cudaMemcpyAsync(dtiles, tl.data(), sizeof(int2) * tl.size(), cudaMemcpyHostToDevice, st));
+  if (dev < 0 || dev >= 64) return fail(WT_ERR_CUDA, "device index %d out of range", dev);
+  {
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    for (int k = 0; k < 2; ++k)
+      if (!g_copy_stream[dev][k]) WT_CUDA(cudaStreamCreateWithFlags(&g_copy_stream[dev][k], cudaStreamNonBlocking));
+  }
+  cudaStream_t sh = g_copy_stream[dev][0], sd = g_copy_stream[dev][1];
+  // every control block at once (pageable memory: a copy per chunk could hold the host thread
+  // until the stream reaches it, and with it the next chunk's copies)
+  WT_CUDA(cudaMemcpyAsync(ctl, hctl.data(), sizeof(Ctl) * nprob, cudaMemcpyHostToDevice, st));
+  EventSet ev;  // [0] start, [1] end, then per chunk: copied in, computed
+  WT_CUDA(ev.make(2 + 2 * K));
+  WT_CUDA(cudaEventRecord(ev.e[0], st));
+  WT_CUDA(cudaStreamWaitEvent(sh, ev.e[0], 0));
+  WT_CUDA(cudaStreamWaitEvent(sd, ev.e[0], 0));
+  auto span = [&](int c, long long& s0, long long& len) {
+    s0 = segs[cb[c]].offset;
+    len = segs[cb[c + 1] - 1].offset + segs[cb[c + 1] - 1].n - s0;
+  };
+  for (int c = 0; c < K; ++c) {
+    const int p0 = cb[c], np = cb[c + 1] - cb[c];
+    cudaStream_t cs = st;
+    long long s0, len;
+    span(c, s0, len);
+    for (int k = 0; k < m; ++k)
+      WT_CUDA(cudaMemcpyAsync(st_u + k * total + s0, u + k * total + s0, sizeof(double) * len, cudaMemcpyHostToDevice,
+                              sh));
+    WT_CUDA(cudaEventRecord(ev.e[2 + 2 * c], sh));
+    WT_CUDA(cudaStreamWaitEvent(cs, ev.e[2 + 2 * c], 0));
+    long long maxn = 0;
+    for (int p = p0; p < p0 + np; ++p) maxn = hs[p].n > maxn ? hs[p].n : maxn;
+    WT_CUDA(launch_pack1d_batched(st_u, total, Un, pitch, dsegs + p0, np, maxn, m, 1, cs));
+    WT_CUDA(prob->mode == WT_MODE_STRICT
+                ? launch_alpha1d_batched_strict(prob->flux, Un, pitch, dsegs + p0, np, maxn, prob->gamma,
+                                                prob->adv_speed, ctl + p0, cs)
+                : launch_alpha1d_batched_fast(prob->flux, Un, pitch, dsegs + p0, np, maxn, prob->gamma,
+                                              prob->adv_speed, ctl + p0, cs));
+    BatchArgs a[3];
+    for (int s2 = 0; s2 < 3; ++s2) {
+      BatchArgs& b = a[s2];
+      memset(&b, 0, sizeof b);
+      b.pitch = pitch;
+      b.segs = dsegs + p0;
+      b.ctl = ctl + p0;
+      b.tiles = dtiles + tb[c];
+      b.ntiles = (int)(tb[c + 1] - tb[c]);
+      b.gamma = prob->gamma;
+      b.adv_speed = prob->adv_speed;
+      b.eps = prob->eps;
+      b.alpha_R = prob->alpha_R;
+    }
+    a[0].uin = Un;
+    a[0].uout = U1;
+    a[1].uin = U1;
+    a[1].un = Un;
+    a[1].uout = U2;
+    a[2].uin = U2;
+    a[2].un = Un;
+    a[2].uout = Un;
+    const int grid = batched_grid_size(prob, tile, tb[c + 1] - tb[c], dev);
+    cudaGraphExec_t exec;
+    int rc;
+    if ((rc = get_batched_graph(prob, dev, tile, grid, a, &exec)) != WT_OK) return rc;
+    for (int64_t i = 0; i < n_steps; ++i) WT_CUDA(cudaGraphLaunch(exec, cs));
+    WT_CUDA(launch_unpack1d_batched(Un, pitch, st_o, total, dsegs + p0, np, maxn, m, cs));
+    WT_CUDA(cudaEventRecord(ev.e[3 + 2 * c], cs));
+    WT_CUDA(cudaStreamWaitEvent(sd, ev.e[3 + 2 * c], 0));
+    for (int k = 0; k < m; ++k)
+      WT_CUDA(cudaMemcpyAsync(u + k * total + s0, st_o + k * total + s0, sizeof(double) * len, cudaMemcpyDeviceToHost,
+                              sd));
+  }
+  WT_CUDA(cudaEventRecord(ev.e[1], sd));
+  WT_CUDA(cudaStreamWaitEvent(st, ev.e[1], 0));
+  std::vector<Ctl> back(nprob);
+  WT_CUDA(cudaMemcpyAsync(back.data(), ctl, sizeof(Ctl) * nprob, cudaMemcpyDeviceToHost, st));
+  WT_CUDA(cudaStreamSynchronize(st));
+  int nfail = 0, first = -1;
+  for (int p = 0; p < nprob; ++p)
+    if (back[p].status != 0 && nfail++ == 0) first = p;
+  if (nfail > 0) {
+    // put the input back: every chunk's part without a status array, else the failed problems'
+    for (int c = 0; c < K; ++c) {
+      long long s0, len;
+      span(c, s0, len);
+      for (int p = cb[c]; p < cb[c + 1]; ++p) {
+        if (s_out && back[p].status == 0) continue;
+        const long long o = s_out ? segs[p].offset : s0, n = s_out ? segs[p].n : len;
+        for (int k = 0; k < m; ++k)
+          WT_CUDA(cudaMemcpyAsync(u + k * total + o, st_u + k * total + o, sizeof(double) * n, cudaMemcpyDeviceToHost,
+                                  st));
+        if (!s_out) break;
+      }
+    }
+    WT_CUDA(cudaStreamSynchronize(st));
+    if (!s_out)
+      return fail(back[first].status, "problem %d: device reported status %d after %lld steps (%d problems failed)",
+                  first, back[first].status, back[first].steps, nfail);
+  }
+  if (t_out) {
+    if (t_dev) {
+      WT_CUDA(launch_gather_t(ctl, nprob, t_out, st));
+    } else {
+      for (int p = 0; p < nprob; ++p) t_out[p] = back[p].t;
+    }
+  }
+  if (s_out) {
+    if (s_dev) {
+      WT_CUDA(launch_gather_status(ctl, nprob, s_out, st));
+    } else {
+      for (int p = 0; p < nprob; ++p) s_out[p] = back[p].status;
+    }
+  }
+  WT_CUDA(cudaStreamSynchronize(st));
+  if (nfail > 0) fail(WT_OK, "%d of %d problems failed (first: problem %d, status %d); see status_per_problem", nfail,
+                      nprob, first, back[first].status);
+  return WT_OK;
+}
+
 int weno_theta_step_batched(const wt_problem* prob, const wt_segment* segs, int32_t nprob, double* u_packed,
                             int64_t total, double cfl, int64_t n_steps, double* t_per_problem,
                             int32_t* status_per_problem, void* ws, size_t ws_bytes, void* stream) {
@@ -1050,25 +1246,6 @@ int weno_theta_step_batched(const wt_problem* prob, const wt_segment* segs, int3
   double* U2 = reinterpret_cast<double*>(w + lay.u2);
   double* st_u = reinterpret_cast<double*>(w + lay.st_u);
 
-  std::vector<Ctl> hctl(nprob, make_ctl(cfl, 0.0, INFINITY));
-  WT_CUDA(cudaMemcpyAsync(dsegs, hs.data(), sizeof(BatchSeg) * nprob, cudaMemcpyHostToDevice, st));
-  const double* src = u_packed;
-  if (!u_dev) {
-    WT_CUDA(cudaMemcpyAsync(st_u, u_packed, sizeof(double) * m * total, cudaMemcpyHostToDevice, st));
-    src = st_u;
-  }
-  WT_CUDA(launch_pack1d_batched(src, total, Un, pitch, dsegs, nprob, maxn, m, 1, st));
-  auto init_ctl = [&]() -> int {
-    WT_CUDA(cudaMemcpyAsync(ctl, hctl.data(), sizeof(Ctl) * nprob, cudaMemcpyHostToDevice, st));
-    WT_CUDA(prob->mode == WT_MODE_STRICT
-                ? launch_alpha1d_batched_strict(prob->flux, Un, pitch, dsegs, nprob, maxn, prob->gamma,
-                                                prob->adv_speed, ctl, st)
-                : launch_alpha1d_batched_fast(prob->flux, Un, pitch, dsegs, nprob, maxn, prob->gamma,
-                                              prob->adv_speed, ctl, st));
-    return WT_OK;
-  };
-  if ((rc = init_ctl()) != WT_OK) return rc;
-
   auto args_for = [&](int ntiles) {
     BatchArgs b;
     memset(&b, 0, sizeof b);
@@ -1101,6 +1278,32 @@ int weno_theta_step_batched(const wt_problem* prob, const wt_segment* segs, int3
           e.pitch == pitch && e.mix == mix)
         tile = e.tile;
   }
+
+  std::vector<Ctl> hctl(nprob, make_ctl(cfl, 0.0, INFINITY));
+  WT_CUDA(cudaMemcpyAsync(dsegs, hs.data(), sizeof(BatchSeg) * nprob, cudaMemcpyHostToDevice, st));
+  double* st_o = reinterpret_cast<double*>(w + lay.st_o);
+  const int nchunk = (!u_dev && tile >= 0 && n_steps > 0) ? pipeline_chunks(segs, nprob, cells, u_packed) : 1;
+  if (nchunk > 1)
+    return step_batched_pipelined(prob, segs, nprob, u_packed, total, n_steps, t_per_problem, t_dev,
+                                  status_per_problem, s_dev, hs, hctl, pitch, tile, nchunk, dev, ctl, dsegs, dtiles,
+                                  Un, U1, U2, st_u, st_o, st);
+  const double* src = u_packed;
+  if (!u_dev) {
+    WT_CUDA(cudaMemcpyAsync(st_u, u_packed, sizeof(double) * m * total, cudaMemcpyHostToDevice, st));
+    src = st_u;
+  }
+  WT_CUDA(launch_pack1d_batched(src, total, Un, pitch, dsegs, nprob, maxn, m, 1, st));
+  auto init_ctl = [&]() -> int {
+    WT_CUDA(cudaMemcpyAsync(ctl, hctl.data(), sizeof(Ctl) * nprob, cudaMemcpyHostToDevice, st));
+    WT_CUDA(prob->mode == WT_MODE_STRICT
+                ? launch_alpha1d_batched_strict(prob->flux, Un, pitch, dsegs, nprob, maxn, prob->gamma,
+                                                prob->adv_speed, ctl, st)
+                : launch_alpha1d_batched_fast(prob->flux, Un, pitch, dsegs, nprob, maxn, prob->gamma,
+                                              prob->adv_speed, ctl, st));
+    return WT_OK;
+  };
+  if ((rc = init_ctl()) != WT_OK) return rc;
+
   if (tile < 0 && n_steps > 0) {
     cudaEvent_t e0, e1;
     WT_CUDA(cudaEventCreate(&e0));

@@ -232,3 +232,54 @@ def test_batched_status_per_problem(wtlib, host):
         b.weno_theta_step_batched(prob, segs, u2, total, 0.5, 8, ws)
     assert e.value.status == b.WT_ERR_NONPHYSICAL
     assert np.array_equal(u2.cpu().numpy(), bad, equal_nan=True)
+
+
+def test_pipelined_host_call_equals_device_call(wtlib, monkeypatch):
+    """On page-locked host arrays of at least 2^23 cells, with the tile already known, a call
+    runs in chunks of problems whose copies overlap other chunks' steps.  Every problem's state
+    and time equal a call on device arrays bit for bit.  A problem that breaks down keeps its
+    input (status array), or the whole input is put back and the call fails (none)."""
+    b = wtlib
+    monkeypatch.setenv("WT_BATCHED_TILE", "5127")  # tile known: the first host call is pipelined
+    batch = W.euler_batch(1024, seed=3)
+    total = int(batch.u.shape[1])
+    assert total >= 2 ** 23  # at least two chunks of 2^22 cells
+    prob = b.problem(b.WT_FLUX_EULER1D, mode=b.WT_MODE_FAST, alpha_R=W.ALPHA_R_SEEDED)
+    segs = _segments(b, batch)
+    nprob = len(segs)
+    ws = b.alloc_workspace(b.workspace_bytes(prob, None, total, nprob))
+    bad = batch.u.copy()
+    last = nprob - 1  # in the last chunk
+    o, n = int(batch.offsets[last]), int(batch.lengths[last])
+    bad[0, o + n // 2] = np.nan
+
+    def device_call(state, status):
+        ud = torch.from_numpy(state.copy()).cuda()
+        td = torch.zeros(nprob, dtype=torch.float64, device="cuda")
+        sd = torch.zeros(nprob, dtype=torch.int32, device="cuda") if status else None
+        b.weno_theta_step_batched(prob, segs, ud, total, 0.5, 6, ws, t_per_problem=td, status_per_problem=sd)
+        torch.cuda.synchronize()
+        return ud.cpu().numpy(), td.cpu().numpy(), None if sd is None else sd.cpu().numpy()
+
+    def host_call(state, status):
+        uh = torch.from_numpy(state.copy()).pin_memory()
+        th = np.zeros(nprob)
+        sh = np.zeros(nprob, dtype=np.int32) if status else None
+        b.weno_theta_step_batched(prob, segs, uh.numpy(), total, 0.5, 6, ws, t_per_problem=th,
+                                  status_per_problem=sh)
+        return uh.numpy().copy(), th, sh
+
+    ud, td, _ = device_call(batch.u, False)
+    uh, th, _ = host_call(batch.u, False)
+    assert np.array_equal(uh, ud) and np.array_equal(th, td)
+    ud, td, sd = device_call(bad, True)
+    uh, th, sh = host_call(bad, True)
+    assert sh[last] == b.WT_ERR_NONPHYSICAL and (np.delete(sh, last) == 0).all()
+    assert np.array_equal(sh, sd) and np.array_equal(th, td)
+    assert np.array_equal(uh, ud, equal_nan=True)
+    assert np.array_equal(uh[:, o:o + n], bad[:, o:o + n], equal_nan=True)
+    uh = torch.from_numpy(bad.copy()).pin_memory()
+    with pytest.raises(b.WenoThetaError) as e:
+        b.weno_theta_step_batched(prob, segs, uh.numpy(), total, 0.5, 6, ws)
+    assert e.value.status == b.WT_ERR_NONPHYSICAL
+    assert np.array_equal(uh.numpy(), bad, equal_nan=True)
