@@ -195,7 +195,8 @@ struct FastMath {
   // one, k = 2, taken as the difference of the two centre cells' products (a2, b2), (a3, b3)),
   // the + side's stencil differences are d_k = da_k + alpha db_k and its q_2 = a2 + alpha b2;
   // the - side reads v- = a - alpha b mirrored, so d_k = alpha db_{4-k} - da_{4-k} and
-  // q_2 = a3 - alpha b3.  Branch-free in `minus`, which may differ between adjacent lanes.
+  // q_2 = a3 - alpha b3.  (The thread pairs of the step-blocked tiles form the - side negated
+  // instead, from products they already hold in that side's order.)
   static constexpr bool kDiffProj = true;
   __device__ __forceinline__ static void side_diffs(const double* da, const double* db, double a2, double b2,
                                                     double a3, double b3, double alpha, bool minus, double* d,
