@@ -35,3 +35,27 @@ def test_reference_arm_uses_the_benchmark_config():
 
     assert bench.config_dict(1)["problems"] == 4096 and bench.config_dict(2)["problems"] == 8192
     assert bench.RK_STEPS == 20 * bench.RK_PER_STEP  # 20 benchmark steps are the whole run
+
+
+def test_kernel_hash_sees_code_not_comments(tmp_path, monkeypatch):
+    """The hash that ties the committed ncu counters to the kernels: a changed comment or blank
+    line keeps it, a changed line of code retires it; every committed counter file matches the
+    current sources."""
+    sys.path.insert(0, ROOT)
+    import shutil
+
+    import bench
+
+    csrc = tmp_path / "paper_1504_00731_gb300" / "csrc"
+    shutil.copytree(os.path.join(ROOT, "paper_1504_00731_gb300", "csrc"), csrc)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    h0 = bench.kernel_hash()
+    f = csrc / "wt_kernels.cuh"
+    text = f.read_text()
+    f.write_text("// a new comment\n\n" + text.replace("// ", "//  ", 3) + "\n/* and a block comment */\n")
+    assert bench.kernel_hash() == h0
+    f.write_text(text.replace("constexpr int kBar = 0;", "constexpr int kBar = 1;", 1))
+    assert bench.kernel_hash() != h0
+    monkeypatch.setattr(bench, "ROOT", ROOT)
+    for kind in bench.COUNTERS:
+        assert bench.counters(kind) is not None, kind
